@@ -1,0 +1,118 @@
+"""Seeded synthetic option batches (input generators only).
+
+This module draws the random inputs of each workload and nothing else: it
+holds none of the method's arithmetic (no Black price, no inversion, no
+adjoint).  Both the CUDA path (bench, tests) and the CPU oracle (tests) take
+their inputs from here, so the two always see identical rows.
+
+The prices P of the synthetic rows are *not* produced here: they come from a
+Black-76 price evaluated by the caller (the oracle in tests, the library's
+``black_price`` in the benchmark), exactly as the paper builds its synthetic
+batches from a known sigma* (Section 4.1, "Gradient correctness").  The only
+prices set here are the boundary quotes of the stress workload, which the
+workload defines directly as a relative offset from the intrinsic value or
+from the upper bound.
+
+Layout: structure of arrays, float64 F, K, T, sigma_star and int8 flag
+(+1 call, -1 put); r = 0 (forward measure), so P is the undiscounted price.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+#: rows in the plain FP64 workload of 4,096 options (ln(K/F) ~ U[-1, 1])
+SMALL_N = 4096
+#: rows in the 16M-option stress workload (ln(K/F) ~ U[-6, 6])
+STRESS_N = 16 * 1024 * 1024
+#: rows in the 64M-option mixed-precision / learned-guess workloads
+LARGE_N = 64 * 1024 * 1024
+
+
+@dataclass
+class Batch:
+    F: np.ndarray
+    K: np.ndarray
+    T: np.ndarray
+    sigma_star: np.ndarray
+    flag: np.ndarray
+    #: price fixed by the workload itself (boundary quotes), NaN elsewhere
+    P_fixed: np.ndarray | None = None
+
+    @property
+    def n(self) -> int:
+        return int(self.F.shape[0])
+
+    def subset(self, idx) -> "Batch":
+        return Batch(self.F[idx], self.K[idx], self.T[idx], self.sigma_star[idx], self.flag[idx],
+                     None if self.P_fixed is None else self.P_fixed[idx])
+
+
+def _flags(rng, n):
+    return np.where(rng.random(n) < 0.5, 1, -1).astype(np.int8)
+
+
+def body_batch(n: int = SMALL_N, seed: int = 1) -> Batch:
+    """F = 100, ln(K/F) ~ U[-1,1], T ~ U[1/365, 3], sigma* ~ U[0.05, 1], calls/puts 50/50.
+
+    The paper's canonical synthetic grid (Section 4.1, Table 1: 1e5 synthetic
+    options; IV band [0.05, 1.0] of Section 2) with 4,096 rows; the same
+    distribution at 64M rows is the mixed-precision workload.
+    """
+    rng = np.random.default_rng(seed)
+    F = np.full(n, 100.0)
+    k = rng.uniform(-1.0, 1.0, n)
+    K = F * np.exp(k)
+    T = rng.uniform(1.0 / 365.0, 3.0, n)
+    sig = rng.uniform(0.05, 1.0, n)
+    return Batch(F, K, T, sig, _flags(rng, n))
+
+
+def stress_batch(n: int = STRESS_N, seed: int = 2, boundary_frac: float = 0.05) -> Batch:
+    """ln(K/F) ~ U[-6,6], s = sigma sqrt(T) log-uniform on [1e-4, 3], T ~ U[1/365, 3].
+
+    A fraction ``boundary_frac`` of quotes sits within 1e-12 relative of a
+    bound of the no-arbitrage interval: half are in-the-money quotes at
+    P = intrinsic * (1 + u 1e-12), half at P = U (1 - u 1e-12) with U = F for
+    calls and K for puts, u ~ U(0, 1].  The paper's low-vega stress chain
+    (Section 4 appendix, "NaN-poisoning diagnostic": deep wings, expiries down
+    to 1e-8 years) motivates the ranges.
+    """
+    rng = np.random.default_rng(seed)
+    F = np.full(n, 100.0)
+    k = rng.uniform(-6.0, 6.0, n)
+    K = F * np.exp(k)
+    T = rng.uniform(1.0 / 365.0, 3.0, n)
+    s = np.exp(rng.uniform(np.log(1e-4), np.log(3.0), n))
+    sig = s / np.sqrt(T)
+    flag = _flags(rng, n)
+    P_fixed = np.full(n, np.nan)
+    nb = int(round(boundary_frac * n))
+    if nb:
+        idx = rng.choice(n, size=nb, replace=False)
+        u = 1.0 - rng.random(nb)  # (0, 1]
+        near_intrinsic = np.arange(nb) < nb // 2
+        i1, u1 = idx[near_intrinsic], u[near_intrinsic]
+        # in the money: a call when F > K, a put otherwise
+        flag[i1] = np.where(F[i1] > K[i1], 1, -1).astype(np.int8)
+        itm = np.where(flag[i1] > 0, F[i1] - K[i1], K[i1] - F[i1])
+        P_fixed[i1] = itm * (1.0 + u1 * 1e-12)
+        i2, u2 = idx[~near_intrinsic], u[~near_intrinsic]
+        upper = np.where(flag[i2] > 0, F[i2], K[i2])
+        P_fixed[i2] = upper * (1.0 - u2 * 1e-12)
+    return Batch(F, K, T, sig, flag, P_fixed)
+
+
+def merge_prices(batch: Batch, P_model: np.ndarray) -> np.ndarray:
+    """Prices of the batch: the workload's fixed boundary quotes where set, else ``P_model``."""
+    if batch.P_fixed is None:
+        return P_model
+    return np.where(np.isnan(batch.P_fixed), P_model, batch.P_fixed)
+
+
+def sample_indices(n: int, m: int, seed: int = 12345) -> np.ndarray:
+    """Deterministic sorted sample of m distinct row indices out of n."""
+    rng = np.random.default_rng(seed)
+    m = min(m, n)
+    return np.sort(rng.choice(n, size=m, replace=False))
