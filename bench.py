@@ -1,0 +1,360 @@
+"""Benchmark: IV inversions/s, forward + backward, on the 16M-option stress batch.
+
+One step = one pivot_iv_forward_backward call over the whole batch (every row
+of the hot path: normalise, LBR boundary, rational guess, Householder(3)
+steps, sigma, gated IFT adjoint), inputs resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--rows R]
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload.  --rows runs a smaller batch of the same
+distribution (profiling only; the default is the full workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2606_17065_gb300 import workloads  # noqa: E402
+
+METRIC = "IV inversions/s fwd+bwd on 1 GB300 (plain FP64, <=1e-13 rel err)"
+UNIT = "inversions/s"
+TAU = 1e-6
+GATE = "nan"
+WORKLOAD = ("stress-16M: ln(K/F)~U[-6,6], sigma*sqrt(T) log-uniform [1e-4,3], T~U[1/365,3], "
+            "5% quotes within 1e-12 rel of intrinsic/upper bound, float64 SoA, fwd+bwd gate=nan tau=1e-6")
+
+# Bytes per row moved by one fused forward+backward: F, K, T, P (4 x 8) + flag (1)
+# in; sigma (8) + status (1) + dP, dF, dK, dT (4 x 8) out.
+BYTES_PER_ROW = 33 + 41
+# FP64 FLOPs per row of the fused kernel on this workload, counted by ncu
+# (smsp__sass_thread_inst_executed_op_{dadd,dmul}_pred_on + 2 x ..._dfma_pred_on,
+# summed over one launch, divided by the rows); see profiles/.  None until counted.
+FLOPS_PER_ROW = None
+# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), None until captured.
+TRAFFIC_PER_ROW = None
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA lanes/clk x 2 FLOP
+# (= 1.25 TFLOP/s nominal at 2.07 GHz), scaled by the SM clock seen under load.
+SMS = 152
+FP64_FLOP_PER_CLK_PER_SM = 4.0
+HBM_PEAK_FALLBACK = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rows", type=int, default=workloads.STRESS_N)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU oracle sample")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        load = [v for v in sm if smax and v > 0.3 * smax] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    rank, world = 0, 1
+    if args.gpus > 1 or "WORLD_SIZE" in os.environ:
+        import torch.distributed as dist
+        world = int(os.environ.get("WORLD_SIZE", args.gpus))
+        rank = int(os.environ.get("RANK", 0))
+        if world > 1:
+            import torch
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(target_seconds: float, seed: int = 2):
+    """Forward+backward rows/s of the CPU oracle on a bounded sample of the stress workload."""
+    import oracle
+    threads = oracle.max_threads()
+    pilot = workloads.stress_batch(4096, seed=seed + 1000)
+    P, _ = oracle.black_price(pilot.F, pilot.K, pilot.T, pilot.sigma_star, pilot.flag, nthreads=threads)
+    P = workloads.merge_prices(pilot, P)
+    t0 = time.perf_counter()
+    sig, _ = oracle.implied_vol(pilot.F, pilot.K, pilot.T, P, pilot.flag, nthreads=threads)
+    oracle.iv_grad(pilot.F, pilot.K, pilot.T, pilot.flag, sig, None, TAU, 1, nthreads=threads)
+    rate = pilot.n / max(time.perf_counter() - t0, 1e-6)
+    n = int(min(max(rate * target_seconds, 4096), 4_000_000))
+    b = workloads.stress_batch(n, seed=seed + 2000)
+    P, _ = oracle.black_price(b.F, b.K, b.T, b.sigma_star, b.flag, nthreads=threads)
+    P = workloads.merge_prices(b, P)
+    t0 = time.perf_counter()
+    sig, _ = oracle.implied_vol(b.F, b.K, b.T, P, b.flag, nthreads=threads)
+    oracle.iv_grad(b.F, b.K, b.T, b.flag, sig, None, TAU, 1, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return n / dt, threads, n, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per_step, threads, n, dt = [], None, None, 0.0
+    if args.warmup > 0:
+        oracle_rate(min(1.0, args.cpu_seconds / 4))
+    for _ in range(max(args.steps, 1)):
+        r, threads, n, d = oracle_rate(args.cpu_seconds / max(args.steps, 1))
+        per_step.append(r)
+        dt += d
+    value = statistics.median(per_step)
+    sample = f"{n} rows of the stress workload per step (seeded), fwd+bwd, oracle with OpenMP"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "rows_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2606_17065_gb300 as pv
+
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    # inputs: this rank's own shard of independent rows (weak scaling)
+    b = workloads.stress_batch(args.rows, seed=2 + rank)
+    n = b.n
+    F = torch.from_numpy(b.F).to(dev)
+    K = torch.from_numpy(b.K).to(dev)
+    T = torch.from_numpy(b.T).to(dev)
+    flag = torch.from_numpy(b.flag).to(dev)
+    P, _ = pv.black_price(F, K, T, torch.from_numpy(b.sigma_star).to(dev), flag, vega=False)
+    fixed = torch.from_numpy(b.P_fixed).to(dev)
+    P = torch.where(torch.isnan(fixed), P, fixed).contiguous()
+    del fixed
+    outs = dict(sigma=torch.empty(n, dtype=torch.float64, device=dev),
+                status=torch.empty(n, dtype=torch.uint8, device=dev),
+                grads=[torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)])
+
+    import ctypes
+    from paper_2606_17065_gb300 import _native
+    lib = _native.lib()
+    p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    opts = _native.PivotOpts()
+    opts.mode, opts.householder = 0, 0
+
+    def step():
+        rc = lib.pivot_iv_forward_backward(n, p(F), p(K), p(T), p(P), p(flag), None, TAU, pv.GATES[GATE],
+                                           p(outs["sigma"]), p(outs["status"]), *[p(g) for g in outs["grads"]],
+                                           ctypes.byref(opts), sptr)
+        if rc != 0:
+            raise RuntimeError(f"pivot_iv_forward_backward failed: {_native.error_string(rc)}")
+
+    def step_fwd():
+        rc = lib.pivot_iv_forward(n, p(F), p(K), p(T), p(P), p(flag), p(outs["sigma"]), p(outs["status"]),
+                                  ctypes.byref(opts), sptr)
+        if rc != 0:
+            raise RuntimeError(f"pivot_iv_forward failed: {_native.error_string(rc)}")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K fused steps, CUDA events on the launching stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(local) as clocks:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for i in range(args.steps):
+            step()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    per_launch = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = max_over_ranks(total_ms, world)
+    ms_per_step = total_ms / args.steps
+    value = n * world / (ms_per_step * 1e-3)
+    clk = clocks.summary()
+
+    # ---- forward-only throughput (same inputs), for context
+    for _ in range(2):
+        step_fwd()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(max(args.steps // 2, 1)):
+        step_fwd()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / max(args.steps // 2, 1)
+
+    # ---- end to end through the public API with pinned host buffers
+    hF, hK, hT, hP = (t.cpu().pin_memory() for t in (F, K, T, P))
+    hflag = flag.cpu().pin_memory()
+    for _ in range(2):
+        pv.iv_forward_backward(hF, hK, hT, hP, hflag, tau=TAU, gate=GATE)
+    torch.cuda.synchronize()
+    e2e_steps = max(min(args.steps, 5), 1)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        res = pv.iv_forward_backward(hF, hK, hT, hP, hflag, tau=TAU, gate=GATE)
+        float(res[0][0])  # results are on the host
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks(e2e_s, world)
+    h2d = n * 33
+    d2h = n * (8 + 1 + 4 * 8)
+
+    # ---- roofline of the fused kernel
+    mean_ms = statistics.mean(per_launch)
+    sm_mhz = clk["sm_mhz"] or 2070.0
+    fp64_peak = SMS * FP64_FLOP_PER_CLK_PER_SM * sm_mhz * 1e6
+    if FLOPS_PER_ROW is not None:
+        achieved = FLOPS_PER_ROW * n / (mean_ms * 1e-3)
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak,
+                "traffic": None if TRAFFIC_PER_ROW is None else TRAFFIC_PER_ROW * n,
+                "flops_per_row": FLOPS_PER_ROW,
+                "peak_source": f"152 SMs x 4 FP64 FLOP/clk (1.25 TFLOP/s nominal at 2.07 GHz) at {sm_mhz:.0f} MHz"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "flops_per_row": None, "peak_source": "FP64 FLOPs per row not yet counted by ncu"}
+    hbm_peak = measured_peaks().get("hbm_gbs", HBM_PEAK_FALLBACK)
+    roof["hbm"] = {"achieved": BYTES_PER_ROW * n / (mean_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                   "frac": BYTES_PER_ROW * n / (mean_ms * 1e-3) / 1e9 / hbm_peak}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        r, threads, m, dt = oracle_rate(args.cpu_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{m} seeded rows of the same stress workload, fwd+bwd, {dt:.1f} s wall"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "rows_per_gpu": n, "parallelism": f"replicas x{world}",
+                           "l2": "inputs 553 MB per step > 129 MB L2: no flush"},
+                "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+                "e2e": {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": args.steps,
+                "roofline": roof,
+                "forward_only": {"value": n * world / (fwd_ms * 1e-3), "unit": UNIT, "ms_per_step": fwd_ms},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

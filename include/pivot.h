@@ -1,0 +1,136 @@
+/*
+ * pivot.h -- C ABI of the PIVOT implied-volatility hot path on GB300 (sm_103a).
+ *
+ * The library inverts undiscounted Black-76 prices (forward measure, r = 0)
+ * to implied volatilities in "Let's Be Rational" form (normalised Black
+ * function, region-wise rational initial guess, Householder(3) refinement) and
+ * supplies the implicit-function-theorem adjoint with the low-vega gating
+ * contract.  Paper: "PIVOT: Bridging Black-Scholes Implied-Volatility and
+ * Price Objectives via Differentiable Jaeckel Operator", Algorithm 1,
+ * Section 3 (forward, backward, low-vega gating) and the appendix on the
+ * five-stage LBR construction.
+ *
+ * Common conventions for every entry point
+ *   - Arrays are structure-of-arrays of length n in DEVICE memory (cudaMalloc,
+ *     torch CUDA tensors or managed memory), owned by the caller.  The
+ *     library allocates nothing and keeps no pointer after the call returns.
+ *   - float64 arrays must be 8-byte aligned; int8/uint8 arrays need no
+ *     alignment.  Input and output arrays must not overlap.
+ *   - F: forward (> 0), K: strike (> 0), T: time to expiry in years (> 0),
+ *     P: undiscounted option price, sigma: annualised volatility,
+ *     flag: +1 call, -1 put.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     is asynchronous on that stream; results are valid once the stream has
+ *     been synchronised.
+ *   - Return value: 0 on success; > 0 an argument error (see PIVOT_E_*),
+ *     nothing was launched; < 0 the negated cudaError_t of a failed launch.
+ *   - n == 0 is valid and launches nothing.
+ *   - Per-row problems are values, not return codes: NaN sigma plus a status
+ *     code (PIVOT_ROW_*), and NaN gradients for invalid rows.
+ */
+#ifndef PIVOT_H
+#define PIVOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define PIVOT_OK 0
+#define PIVOT_E_SIZE 1        /* n < 0 */
+#define PIVOT_E_NULL 2        /* a required pointer is NULL */
+#define PIVOT_E_GATE 3        /* gate_mode outside 0..3, tau < 0 or NaN, or tau == 0 with the smooth gate */
+#define PIVOT_E_OPTS 4        /* bad pivot_opts field */
+#define PIVOT_E_NOT_DEVICE 5  /* a pointer is not accessible from the current device */
+#define PIVOT_E_ALIGN 6       /* a float64 pointer is not 8-byte aligned */
+
+/* ---- per-row status codes (uint8) --------------------------------------- */
+#define PIVOT_ROW_OK 0              /* sigma finite and > 0 */
+#define PIVOT_ROW_BELOW_INTRINSIC 1 /* P < intrinsic value: sigma = NaN (Section 3.1) */
+#define PIVOT_ROW_ABOVE_UPPER 2     /* P > F (call) or K (put), super-arbitrage: sigma = NaN */
+#define PIVOT_ROW_BAD_INPUT 3       /* non-finite input, F, K or T <= 0, flag not +-1: sigma = NaN */
+#define PIVOT_ROW_AT_INTRINSIC 4    /* P equals the intrinsic value: sigma = 0 */
+#define PIVOT_ROW_AT_UPPER 5        /* P equals the upper bound: sigma = +inf */
+
+/* ---- gate modes of the backward (Section 3.3, Eq. wellcond_set, smooth_gate) ---- */
+#define PIVOT_GATE_EXACT 0  /* the exact IFT value on every valid row */
+#define PIVOT_GATE_NAN 1    /* exact on G_tau = {|V| > tau}; off G_tau 0 where the cotangent is 0, else NaN */
+#define PIVOT_GATE_MASK 2   /* exact on G_tau, 0 off G_tau (hard mask 1{|V| > tau}) */
+#define PIVOT_GATE_SMOOTH 3 /* every row times w_tau(V) = V^2 / (V^2 + tau^2) */
+
+/* ---- forward variants ----------------------------------------------------- */
+#define PIVOT_MODE_FP64 0   /* plain FP64 throughout */
+#define PIVOT_MODE_MIXED 1  /* FP32 guess and first Householder step, FP64 final step */
+
+typedef struct {
+  int32_t mode;        /* PIVOT_MODE_* ; default PIVOT_MODE_FP64 */
+  int32_t householder; /* Householder(3) iterations after the initial guess, 0 = default (2), max 4 */
+} pivot_opts;
+
+/*
+ * pivot_black_price -- undiscounted Black-76 price with r = 0 (Eq. app_black76)
+ * and vega V = F phi(d1) sqrt(T) (Eq. app_vega_closed_form).
+ *   in : F, K, T, sigma (n float64), flag (n int8)
+ *   out: P_out (n float64); vega_out (n float64, may be NULL)
+ * sigma = 0 gives the intrinsic value, sigma = +inf the upper bound; invalid
+ * rows (non-finite, F/K/T <= 0, sigma < 0, bad flag) give NaN.
+ */
+int pivot_black_price(int64_t n, const double* F, const double* K, const double* T,
+                      const double* sigma, const int8_t* flag, double* P_out,
+                      double* vega_out, void* stream);
+
+/*
+ * pivot_iv_forward -- implied volatility, Algorithm 1 (forward): normalise to
+ * (x, beta) with beta = (P - intrinsic)/sqrt(F K), solve b(x, s) = beta in LBR
+ * form (appendix stages 1-5), return sigma = s / sqrt(T).
+ *   in : F, K, T, P (n float64), flag (n int8)
+ *   out: sigma_out (n float64); status_out (n uint8, may be NULL)
+ *   opts: may be NULL (plain FP64, 2 Householder steps)
+ */
+int pivot_iv_forward(int64_t n, const double* F, const double* K, const double* T,
+                     const double* P, const int8_t* flag, double* sigma_out,
+                     uint8_t* status_out, const pivot_opts* opts, void* stream);
+
+/*
+ * pivot_iv_backward -- vector-Jacobian product of sigma(P, F, K, T), Algorithm 1
+ * (backward) and Eq. method_vjp:
+ *   dP = gbar / V,  dF = -gbar (dP_B/dF) / V,  dK = -gbar (dP_B/dK) / V,
+ *   dT = -gbar sigma / (2 T),
+ * recomputed from the saved (F, K, T, flag, sigma) only (Section 3.2), then
+ * gated per gate_mode with threshold tau (cash vega units).
+ *   in : F, K, T, sigma (n float64), flag (n int8),
+ *        gbar (n float64 upstream cotangent; NULL means 1 on every row, i.e.
+ *        the diagonal of the Jacobian), tau >= 0, gate_mode PIVOT_GATE_*
+ *   out: dP, dF, dK, dT (n float64 each, any may be NULL to skip)
+ * Rows with NaN sigma give NaN.  Rows with sigma = 0 or +inf sit on a bound of
+ * the price interval (V = 0, outside every G_tau): NaN in the exact mode,
+ * otherwise the off-G_tau value of the gate.
+ */
+int pivot_iv_backward(int64_t n, const double* F, const double* K, const double* T,
+                      const int8_t* flag, const double* sigma, const double* gbar,
+                      double tau, int32_t gate_mode, double* dP, double* dF, double* dK,
+                      double* dT, void* stream);
+
+/*
+ * pivot_iv_forward_backward -- both of the above in one pass over HBM: the
+ * forward result and its gated adjoint, same conventions.  sigma_out is
+ * required; status_out and each gradient output may be NULL.
+ */
+int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const double* T,
+                              const double* P, const int8_t* flag, const double* gbar,
+                              double tau, int32_t gate_mode, double* sigma_out,
+                              uint8_t* status_out, double* dP, double* dF, double* dK,
+                              double* dT, const pivot_opts* opts, void* stream);
+
+/* Human-readable text for a return code. */
+const char* pivot_error_string(int code);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int pivot_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIVOT_H */

@@ -1,0 +1,174 @@
+"""Torch-facing API over the C ABI (include/pivot.h).
+
+PyTorch provides device memory and the current CUDA stream; every step of the
+computation runs in the library's CUDA kernels.  Inputs may be CUDA tensors
+(used in place when already float64 / int8 and contiguous) or CPU tensors, in
+which case they are copied to the current CUDA device and the results copied
+back (the end-to-end path).  There is no CPU implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native
+
+ROW_OK, ROW_BELOW_INTRINSIC, ROW_ABOVE_UPPER, ROW_BAD_INPUT, ROW_AT_INTRINSIC, ROW_AT_UPPER = range(6)
+GATES = {"exact": 0, "nan": 1, "mask": 2, "smooth": 3}
+MODES = {"fp64": 0, "mixed": 1}
+
+
+def _gate(gate) -> int:
+    if isinstance(gate, str):
+        if gate not in GATES:
+            raise ValueError(f"gate must be one of {sorted(GATES)}")
+        return GATES[gate]
+    return int(gate)
+
+
+def _device_of(*ts):
+    for t in ts:
+        if isinstance(t, torch.Tensor) and t.is_cuda:
+            return t.device
+    if not torch.cuda.is_available():
+        raise RuntimeError("pivot needs a CUDA device (no CPU fallback)")
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def _on(t, device, dtype):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(t)
+    if t.device != device:
+        t = t.to(device, non_blocking=True)
+    if t.dtype != dtype:
+        t = t.to(dtype)
+    return t.contiguous()
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _host_result(inputs, outs):
+    """Copy outputs back to the host when every given input was a host tensor."""
+    host = all((not isinstance(t, torch.Tensor)) or not t.is_cuda for t in inputs if t is not None)
+    if not host:
+        return outs
+    res = []
+    for o in outs:
+        if o is None:
+            res.append(None)
+            continue
+        h = torch.empty(o.shape, dtype=o.dtype, pin_memory=True)
+        h.copy_(o, non_blocking=True)
+        res.append(h)
+    torch.cuda.current_stream(outs[0].device).synchronize()
+    return res
+
+
+def _check_lengths(n, *ts):
+    for t in ts:
+        if t is not None and t.numel() != n:
+            raise ValueError("all arrays must have the same length")
+
+
+def black_price(F, K, T, sigma, flag, *, vega: bool = True):
+    """Undiscounted Black-76 price (r = 0) and vega; returns (P, vega or None)."""
+    dev = _device_of(F, K, T, sigma, flag)
+    f, k, t, s = (_on(a, dev, torch.float64) for a in (F, K, T, sigma))
+    fl = _on(flag, dev, torch.int8)
+    n = f.numel()
+    _check_lengths(n, k, t, s, fl)
+    P = torch.empty(n, dtype=torch.float64, device=dev)
+    V = torch.empty(n, dtype=torch.float64, device=dev) if vega else None
+    _native.call("pivot_black_price", n, _p(f), _p(k), _p(t), _p(s), _p(fl), _p(P), _p(V), _stream(dev))
+    return tuple(_host_result((F, K, T, sigma, flag), [P, V]))
+
+
+def _opts(mode, householder):
+    o = _native.PivotOpts()
+    o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    o.householder = int(householder)
+    return o
+
+
+def iv(F, K, T, P, flag, *, mode="fp64", householder: int = 0, status: bool = True):
+    """Implied volatility (Algorithm 1 forward); returns (sigma, status or None)."""
+    dev = _device_of(F, K, T, P, flag)
+    f, k, t, p = (_on(a, dev, torch.float64) for a in (F, K, T, P))
+    fl = _on(flag, dev, torch.int8)
+    n = f.numel()
+    _check_lengths(n, k, t, p, fl)
+    sig = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev) if status else None
+    o = _opts(mode, householder)
+    _native.call("pivot_iv_forward", n, _p(f), _p(k), _p(t), _p(p), _p(fl), _p(sig), _p(st), ctypes.byref(o),
+                 _stream(dev))
+    return tuple(_host_result((F, K, T, P, flag), [sig, st]))
+
+
+def iv_backward(F, K, T, flag, sigma, gbar=None, *, tau: float = 1e-6, gate="nan"):
+    """Gated IFT vector-Jacobian product (Eq. method_vjp, Section 3.3); returns (dP, dF, dK, dT)."""
+    dev = _device_of(F, K, T, flag, sigma, gbar)
+    f, k, t, s = (_on(a, dev, torch.float64) for a in (F, K, T, sigma))
+    fl = _on(flag, dev, torch.int8)
+    g = _on(gbar, dev, torch.float64)
+    n = f.numel()
+    _check_lengths(n, k, t, s, fl, g)
+    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
+    _native.call("pivot_iv_backward", n, _p(f), _p(k), _p(t), _p(fl), _p(s), _p(g), float(tau), _gate(gate),
+                 *[_p(o) for o in outs], _stream(dev))
+    return tuple(_host_result((F, K, T, flag, sigma, gbar), outs))
+
+
+def iv_forward_backward(F, K, T, P, flag, gbar=None, *, tau: float = 1e-6, gate="nan", mode="fp64",
+                        householder: int = 0):
+    """Forward and gated adjoint in one pass; returns (sigma, status, dP, dF, dK, dT)."""
+    dev = _device_of(F, K, T, P, flag, gbar)
+    f, k, t, p = (_on(a, dev, torch.float64) for a in (F, K, T, P))
+    fl = _on(flag, dev, torch.int8)
+    g = _on(gbar, dev, torch.float64)
+    n = f.numel()
+    _check_lengths(n, k, t, p, fl, g)
+    sig = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
+    o = _opts(mode, householder)
+    _native.call("pivot_iv_forward_backward", n, _p(f), _p(k), _p(t), _p(p), _p(fl), _p(g), float(tau),
+                 _gate(gate), _p(sig), _p(st), *[_p(x) for x in outs], ctypes.byref(o), _stream(dev))
+    return tuple(_host_result((F, K, T, P, flag, gbar), [sig, st, *outs]))
+
+
+class ImpliedVol(torch.autograd.Function):
+    """sigma = JaeckelIV(P; F, K, T, flag) as an autograd node (Algorithm 1, Section 3.2).
+
+    Forward runs the CUDA LBR solver with gradients suppressed and saves only
+    (F, K, T, flag, sigma); backward returns the gated IFT VJP for P, F, K, T.
+    """
+
+    @staticmethod
+    def forward(ctx, P, F, K, T, flag, tau=1e-6, gate="nan"):
+        sig, _ = iv(F.detach(), K.detach(), T.detach(), P.detach(), flag, status=False)
+        ctx.save_for_backward(F.detach(), K.detach(), T.detach(), flag, sig)
+        ctx.tau, ctx.gate = float(tau), gate
+        return sig
+
+    @staticmethod
+    def backward(ctx, gsig):
+        F, K, T, flag, sig = ctx.saved_tensors
+        dP, dF, dK, dT = iv_backward(F, K, T, flag, sig, gsig.contiguous(), tau=ctx.tau, gate=ctx.gate)
+        need = ctx.needs_input_grad
+        return (dP if need[0] else None, dF if need[1] else None, dK if need[2] else None,
+                dT if need[3] else None, None, None, None)
+
+
+def implied_volatility_autograd(P, F, K, T, flag, tau: float = 1e-6, gate="nan"):
+    """Differentiable implied volatility (the paper's operator), see ``ImpliedVol``."""
+    return ImpliedVol.apply(P, F, K, T, flag, tau, gate)

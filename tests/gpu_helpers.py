@@ -1,0 +1,77 @@
+"""Shared helpers for the GPU parity tests (inputs from workloads, truth from the oracle)."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2606_17065_gb300 import workloads
+
+EPS = float(np.finfo(np.float64).eps)
+DEV = torch.device("cuda", 0)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def oracle_inputs(batch, nthreads=0):
+    """Prices of a batch from the oracle's Black price (plus the workload's fixed boundary quotes)."""
+    P, _ = oracle.black_price(batch.F, batch.K, batch.T, batch.sigma_star, batch.flag, nthreads=nthreads)
+    return workloads.merge_prices(batch, P)
+
+
+def conditioning(F, K, T, P, flag, sig):
+    """kappa_P = P/(sigma V) and kappa_beta = tv/(sigma V), V the vega at sigma (oracle)."""
+    _, V = oracle.black_price(F, K, T, np.where(np.isfinite(sig), sig, 1.0), flag, nthreads=0)
+    itm = np.where(flag > 0, np.maximum(F - K, 0.0), np.maximum(K - F, 0.0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kp = P / (sig * V)
+        kb = (P - itm) / (sig * V)
+    return kp, kb
+
+
+def exponent(F, K, T, sig):
+    """A + B = x^2/(2 s^2) + s^2/8: the conditioning of b_s in its arguments."""
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        s = sig * np.sqrt(T)
+        x = np.log(F / K)
+        return 0.5 * (x / s) ** 2 + 0.125 * s * s
+
+
+def assert_sigma_parity(F, K, T, P, flag, sig, st, ref, st_ref, tol=1e-13, where=""):
+    """Status identical on every row; sigma within `tol` relative on the parity domain
+    (status 0, kappa_P <= 100); elsewhere within a conditioning-scaled bound."""
+    assert np.array_equal(st, st_ref), f"{where}: status mismatch on {np.sum(st != st_ref)} rows"
+    ok = st_ref == 0
+    assert np.array_equal(np.isnan(sig), np.isnan(ref)), f"{where}: NaN pattern differs"
+    assert np.all(sig[st_ref == 4] == 0) and np.all(np.isinf(sig[st_ref == 5]))
+    kp, kb = conditioning(F, K, T, P, flag, ref)
+    rel = np.abs(sig - ref) / ref
+    dom = ok & (kp <= 100)
+    if dom.any():
+        worst = rel[dom].max()
+        assert worst <= tol, f"{where}: max rel sigma error {worst:.3e} on the parity domain"
+    off = ok & ~dom
+    if off.any():
+        bound = 256 * EPS * (1 + kb[off])
+        bad = rel[off] > bound
+        assert not bad.any(), f"{where}: {bad.sum()} off-domain rows beyond the conditioning bound"
+    return dom
+
+
+def assert_grad_parity(got, want, rows, tol=1e-10, where=""):
+    """Identical non-finite pattern; finite values within `tol` relative on `rows`."""
+    for name, g, w in zip(("dP", "dF", "dK", "dT"), got, want):
+        g, w = g[rows], w[rows]
+        assert np.array_equal(np.isnan(g), np.isnan(w)), f"{where} {name}: NaN pattern differs"
+        assert np.array_equal(np.isinf(g), np.isinf(w)), f"{where} {name}: inf pattern differs"
+        fin = np.isfinite(w)
+        denom = np.maximum(np.abs(w[fin]), 1e-300)
+        rel = np.abs(g[fin] - w[fin]) / denom
+        if rel.size:
+            assert rel.max() <= tol, f"{where} {name}: max rel error {rel.max():.3e}"

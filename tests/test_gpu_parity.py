@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: status codes identical on every row; sigma within 1e-13 relative and
+gradients within 1e-10 relative on the parity domain (status 0 and
+kappa_P = P/(sigma V) <= 100); elsewhere sigma within a bound scaled by the
+conditioning kappa_beta = (P - intrinsic)/(sigma V) of the time value.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_2606_17065_gb300 as pv  # noqa: E402
+from paper_2606_17065_gb300 import _native, workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+from gpu_helpers import (DEV, EPS, assert_grad_parity, assert_sigma_parity, conditioning, oracle_inputs,  # noqa: E402
+                         to_dev, to_np)
+
+
+@pytest.fixture(scope="module")
+def body():
+    b = workloads.body_batch(workloads.SMALL_N, seed=1)
+    P = oracle_inputs(b)
+    ref, st = oracle.implied_vol(b.F, b.K, b.T, P, b.flag, nthreads=0)
+    return b, P, ref, st
+
+
+@pytest.fixture(scope="module")
+def stress():
+    b = workloads.stress_batch(65536, seed=2)
+    P = oracle_inputs(b)
+    ref, st = oracle.implied_vol(b.F, b.K, b.T, P, b.flag, nthreads=0)
+    return b, P, ref, st
+
+
+def gpu_iv(b, P, **kw):
+    sig, st = pv.iv(to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(P), to_dev(b.flag), **kw)
+    torch.cuda.synchronize()
+    return to_np(sig), to_np(st)
+
+
+def test_black_price_parity():
+    for b in (workloads.body_batch(20000, seed=3), workloads.stress_batch(20000, seed=4, boundary_frac=0.0)):
+        P, V = pv.black_price(to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(b.sigma_star), to_dev(b.flag))
+        Pr, Vr = oracle.black_price(b.F, b.K, b.T, b.sigma_star, b.flag, nthreads=0)
+        P, V = to_np(P), to_np(V)
+        s = b.sigma_star * np.sqrt(b.T)
+        cond = 1 + 0.5 * (np.log(b.F / b.K) / s) ** 2 + s * s / 8
+        tiny = Pr < 1e-300
+        relP = np.abs(P - Pr) / np.maximum(Pr, 1e-300)
+        assert np.all(relP[~tiny] <= 32 * EPS * cond[~tiny])
+        relV = np.abs(V - Vr) / np.maximum(Vr, 1e-300)
+        assert np.all(relV[Vr > 1e-300] <= 32 * EPS * cond[Vr > 1e-300])
+
+
+def test_forward_parity_body(body):
+    b, P, ref, st_ref = body
+    sig, st = gpu_iv(b, P)
+    dom = assert_sigma_parity(b.F, b.K, b.T, P, b.flag, sig, st, ref, st_ref, where="body")
+    assert dom.mean() > 0.85
+
+
+def test_forward_parity_stress(stress):
+    b, P, ref, st_ref = stress
+    sig, st = gpu_iv(b, P)
+    dom = assert_sigma_parity(b.F, b.K, b.T, P, b.flag, sig, st, ref, st_ref, where="stress")
+    assert dom.sum() > 10000
+
+
+@pytest.mark.parametrize("steps", [2, 3, 4])
+def test_householder_steps(body, steps):
+    b, P, ref, st_ref = body
+    sig, st = gpu_iv(b, P, householder=steps)
+    assert_sigma_parity(b.F, b.K, b.T, P, b.flag, sig, st, ref, st_ref, where=f"steps={steps}")
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_backward_parity(body, stress, mode):
+    for name, (b, P, ref, st_ref) in (("body", body), ("stress", stress)):
+        rng = np.random.default_rng(mode)
+        g = rng.normal(size=b.n)
+        g[::5] = 0.0
+        kp, _ = conditioning(b.F, b.K, b.T, P, b.flag, ref)
+        _, Vr = oracle.black_price(b.F, b.K, b.T, np.where(np.isfinite(ref), ref, 1.0), b.flag, nthreads=0)
+        tau = float(np.median(Vr[st_ref == 0])) * 0.1
+        want = oracle.iv_grad(b.F, b.K, b.T, b.flag, ref, g, tau, mode, nthreads=0)
+        got = pv.iv_backward(to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(b.flag), to_dev(ref), to_dev(g),
+                             tau=tau, gate=mode)
+        got = [to_np(x) for x in got]
+        # same sigma on both sides: every row is compared
+        assert_grad_parity(got, want, np.ones(b.n, bool), where=f"{name} mode={mode}")
+
+
+def test_forward_backward_fused_parity(body, stress):
+    for name, (b, P, ref, st_ref) in (("body", body), ("stress", stress)):
+        tau = 1e-6
+        out = pv.iv_forward_backward(to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(P), to_dev(b.flag), tau=tau,
+                                     gate="nan")
+        sig, st, *grads = [to_np(x) for x in out]
+        dom = assert_sigma_parity(b.F, b.K, b.T, P, b.flag, sig, st, ref, st_ref, where=f"fused {name}")
+        want = oracle.iv_grad(b.F, b.K, b.T, b.flag, ref, None, tau, 1, nthreads=0)
+        assert_grad_parity(grads, want, dom, where=f"fused {name}")
+        # sigma from the separate forward is the same bits
+        sig2, _ = gpu_iv(b, P)
+        assert np.array_equal(sig, sig2, equal_nan=True)
+
+
+def edge_rows():
+    F, K, T, P, flag = [], [], [], [], []
+
+    def add(f, k, t, p, fl):
+        F.append(f); K.append(k); T.append(t); P.append(p); flag.append(fl)
+
+    add(100.0, 100.0, 1.0, 7.96, 1)          # at the money
+    add(100.0, 100.0, 1.0, 7.96, -1)
+    add(100.0, 100.0 * (1 + 1e-12), 0.5, 3.0, 1)  # |x| ~ 1e-12
+    add(100.0, 100.0, 1.0, 1e-300, 1)        # ATM, tiny price
+    add(100.0, 100.0, 1.0, 99.999999, 1)     # ATM, price near the upper bound
+    add(100.0, 120.0, 1.0, 0.0, 1)           # OTM call at zero: at intrinsic
+    add(100.0, 80.0, 1.0, 20.0, 1)           # ITM call at intrinsic
+    add(100.0, 80.0, 1.0, 20.0 + 1e-10, 1)   # just above intrinsic
+    add(100.0, 80.0, 1.0, 19.9, 1)           # below intrinsic
+    add(100.0, 80.0, 1.0, 100.0, 1)          # at the upper bound F
+    add(100.0, 80.0, 1.0, 100.5, 1)          # above the upper bound
+    add(100.0, 80.0, 1.0, 80.0, -1)          # put at the upper bound K
+    add(100.0, 80.0, 1.0, 79.9999999, -1)    # put just below the upper bound: huge sigma
+    add(100.0, 150.0, 1e-8, 1e-200, 1)       # tiny T, deep OTM
+    add(100.0, 60.0, 2.0, 1e-310, -1)        # subnormal price
+    add(100.0, 100.0 * np.exp(-6), 3.0, 99.7, 1)  # deep ITM, price near F
+    add(100.0, 100.0, 0.0, 5.0, 1)           # T = 0
+    add(-1.0, 100.0, 1.0, 5.0, 1)            # F < 0
+    add(100.0, 100.0, 1.0, np.nan, 1)        # NaN price
+    add(100.0, np.inf, 1.0, 5.0, 1)          # inf strike
+    add(100.0, 100.0, 1.0, 5.0, 0)           # bad flag
+    add(100.0, 100.0, 1.0, 5.0, 3)           # bad flag
+    add(1e-100, 1e-100, 1.0, 3e-102, 1)      # tiny scale
+    add(1e100, 2e100, 1.0, 1e98, -1)         # large scale
+    add(100.0, 100.0 * np.exp(0.3), 1.0, 1e-3, 1)
+    add(100.0, 100.0 * np.exp(-0.3), 1.0, 30.0 + 1e-3, 1)
+    return (np.array(F), np.array(K), np.array(T), np.array(P), np.array(flag, np.int8))
+
+
+def test_edge_cases():
+    F, K, T, P, flag = edge_rows()
+    ref, st_ref = oracle.implied_vol(F, K, T, P, flag)
+    sig, st = pv.iv(to_dev(F), to_dev(K), to_dev(T), to_dev(P), to_dev(flag))
+    sig, st = to_np(sig), to_np(st)
+    assert_sigma_parity(F, K, T, P, flag, sig, st, ref, st_ref, where="edge")
+    for mode in range(4):
+        want = oracle.iv_grad(F, K, T, flag, ref, None, 1e-6, mode)
+        got = [to_np(x) for x in pv.iv_backward(to_dev(F), to_dev(K), to_dev(T), to_dev(flag), to_dev(ref),
+                                                 tau=1e-6, gate=mode)]
+        kp, _ = conditioning(F, K, T, P, flag, ref)
+        rows = ~((st_ref == 0) & ~(kp <= 100))  # skip ill-conditioned finite rows
+        assert_grad_parity(got, want, rows, where=f"edge mode={mode}")
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 255, 257, 4097])
+def test_ragged_sizes(n):
+    b = workloads.body_batch(n, seed=100 + n)
+    P = oracle_inputs(b)
+    ref, st_ref = oracle.implied_vol(b.F, b.K, b.T, P, b.flag)
+    sig, st = gpu_iv(b, P)
+    assert sig.shape == (n,)
+    assert_sigma_parity(b.F, b.K, b.T, P, b.flag, sig, st, ref, st_ref, where=f"n={n}")
+
+
+def test_empty_batch():
+    e = torch.empty(0, dtype=torch.float64, device=DEV)
+    sig, st = pv.iv(e, e, e, e, torch.empty(0, dtype=torch.int8, device=DEV))
+    assert sig.numel() == 0 and st.numel() == 0
+
+
+def test_capi_argument_errors():
+    lib = _native.lib()
+    n = 8
+    d = torch.ones(n, dtype=torch.float64, device=DEV)
+    fl = torch.ones(n, dtype=torch.int8, device=DEV)
+    out = torch.empty(n, dtype=torch.float64, device=DEV)
+    host = torch.ones(n, dtype=torch.float64)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.pivot_iv_forward(-1, p(d), p(d), p(d), p(d), p(fl), p(out), None, None, s) == 1
+    assert lib.pivot_iv_forward(n, None, p(d), p(d), p(d), p(fl), p(out), None, None, s) == 2
+    assert lib.pivot_iv_forward(n, p(host), p(d), p(d), p(d), p(fl), p(out), None, None, s) == 5
+    mis = ctypes.c_void_p(d.data_ptr() + 4)
+    assert lib.pivot_iv_forward(n - 1, mis, p(d), p(d), p(d), p(fl), p(out), None, None, s) == 6
+    bad = _native.PivotOpts()
+    bad.mode, bad.householder = 0, 9
+    assert lib.pivot_iv_forward(n, p(d), p(d), p(d), p(d), p(fl), p(out), None, ctypes.byref(bad), s) == 4
+    assert lib.pivot_iv_backward(n, p(d), p(d), p(d), p(fl), p(d), None, -1.0, 1, p(out), None, None, None, s) == 3
+    assert lib.pivot_iv_backward(n, p(d), p(d), p(d), p(fl), p(d), None, 0.0, 3, p(out), None, None, None, s) == 3
+    assert lib.pivot_iv_backward(n, p(d), p(d), p(d), p(fl), p(d), None, 1e-6, 7, p(out), None, None, None, s) == 3
+    assert lib.pivot_iv_forward(0, None, None, None, None, None, None, None, None, s) == 0
+    with pytest.raises(_native.PivotError):
+        pv.iv(host.to(DEV), d, d, d, fl, mode=5)
+
+
+def test_host_tensors_round_trip(body):
+    """The end-to-end path: host tensors in, host tensors out."""
+    b, P, ref, st_ref = body
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    sig, st = pv.iv(t(b.F), t(b.K), t(b.T), t(P), t(b.flag))
+    assert not sig.is_cuda
+    assert_sigma_parity(b.F, b.K, b.T, P, b.flag, sig.numpy(), st.numpy(), ref, st_ref, where="host")
+
+
+def test_full_size_stress_sampled():
+    """16M stress rows in the benchmark's launch configuration; sampled rows checked one by one."""
+    b = workloads.stress_batch(workloads.STRESS_N, seed=2)
+    F, K, T, flag = to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(b.flag)
+    P_dev, _ = pv.black_price(F, K, T, to_dev(b.sigma_star), flag, vega=False)
+    fixed = torch.from_numpy(b.P_fixed).to(DEV)
+    P_dev = torch.where(torch.isnan(fixed), P_dev, fixed)
+    idx = workloads.sample_indices(b.n, 20000, seed=9)
+    sb = b.subset(idx)
+    P_s = oracle_inputs(sb)  # the oracle's own prices on the sampled rows
+    P_dev[torch.from_numpy(idx).to(DEV)] = torch.from_numpy(P_s).to(DEV)
+    sig, st, dP, dF, dK, dT = pv.iv_forward_backward(F, K, T, P_dev, flag, tau=1e-6, gate="nan")
+    torch.cuda.synchronize()
+    ref, st_ref = oracle.implied_vol(sb.F, sb.K, sb.T, P_s, sb.flag, nthreads=0)
+    sig_s, st_s = to_np(sig[torch.from_numpy(idx).to(DEV)]), to_np(st[torch.from_numpy(idx).to(DEV)])
+    dom = assert_sigma_parity(sb.F, sb.K, sb.T, P_s, sb.flag, sig_s, st_s, ref, st_ref, where="16M sample")
+    want = oracle.iv_grad(sb.F, sb.K, sb.T, sb.flag, ref, None, 1e-6, 1, nthreads=0)
+    got = [to_np(g[torch.from_numpy(idx).to(DEV)]) for g in (dP, dF, dK, dT)]
+    assert_grad_parity(got, want, dom, where="16M sample")
+    # properties over every row: status in range, sigma finite and > 0 exactly on status 0
+    st_all = to_np(st)
+    sig_all = to_np(sig)
+    assert st_all.max() <= 5
+    ok = st_all == 0
+    assert np.all(np.isfinite(sig_all[ok]) & (sig_all[ok] > 0))
+    assert np.all(np.isnan(sig_all[np.isin(st_all, [1, 2, 3])]))
