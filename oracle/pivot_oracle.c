@@ -409,7 +409,7 @@ static double solve_s(const solve_t* q) {
     /* bisect (geometrically) when Newton leaves the bracket or stalls */
     if (!newton_ok || fabs(g) > 0.5 * gprev) {
       if (lo > 0.0 && isfinite(hi)) sn = sqrt(lo) * sqrt(hi);
-      else if (isfinite(hi)) sn = 0.5 * hi;
+      else if (isfinite(hi)) sn = hi < 0.5 ? hi * hi : 0.5 * hi; /* roots reach ~1e-320 */
       else sn = 2.0 * s;
       if (!(sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
     }

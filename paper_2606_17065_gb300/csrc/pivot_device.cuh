@@ -142,11 +142,17 @@ __device__ __forceinline__ double time_value_itm(double P, double a, double b) {
   return s2 + (e1 + e2);
 }
 
-// x = -|ln(F/K)| with relative accuracy near the money, b_max = e^{x/2}
+// -|ln(F/K)| from mn = min(F, K), mx = max(F, K): within a factor 2, mx - mn
+// is exact (Sterbenz) and log1p keeps the relative accuracy near the money;
+// further out, the ratio itself is accurate.
+__device__ __forceinline__ double neg_abs_log_ratio(double mn, double mx) {
+  return (mn >= 0.5 * mx) ? log1p(-(mx - mn) / mx) : log(mn / mx);
+}
+
+// x = -|ln(F/K)|, b_max = e^{x/2} = sqrt(min/max)
 __device__ __forceinline__ void moneyness(double F, double K, double& x, double& bmax) {
   const double mn = fmin(F, K), mx = fmax(F, K);
-  const double delta = (mx - mn) / mx; // mx - mn exact within a factor 2 (Sterbenz)
-  x = log1p(-delta);
+  x = neg_abs_log_ratio(mn, mx);
   bmax = sqrt(mn / mx);
 }
 
@@ -325,8 +331,7 @@ struct Grad {
 };
 
 __device__ __forceinline__ double signed_log_moneyness(double F, double K) {
-  const double mn = fmin(F, K), mx = fmax(F, K);
-  const double l = log1p(-(mx - mn) / mx); // -|ln(F/K)|
+  const double l = neg_abs_log_ratio(fmin(F, K), fmax(F, K)); // -|ln(F/K)|
   return F >= K ? -l : l;
 }
 

@@ -93,7 +93,7 @@ def test_backward_parity(body, stress, mode):
                              tau=tau, gate=mode)
         got = [to_np(x) for x in got]
         # same sigma on both sides: every row is compared
-        assert_grad_parity(got, want, np.ones(b.n, bool), where=f"{name} mode={mode}")
+        assert_grad_parity(got, want, np.ones(b.n, bool), where=f"{name} mode={mode}", vega=Vr, gbar=g)
 
 
 def test_forward_backward_fused_parity(body, stress):
@@ -155,9 +155,8 @@ def test_edge_cases():
         want = oracle.iv_grad(F, K, T, flag, ref, None, 1e-6, mode)
         got = [to_np(x) for x in pv.iv_backward(to_dev(F), to_dev(K), to_dev(T), to_dev(flag), to_dev(ref),
                                                  tau=1e-6, gate=mode)]
-        kp, _ = conditioning(F, K, T, P, flag, ref)
-        rows = ~((st_ref == 0) & ~(kp <= 100))  # skip ill-conditioned finite rows
-        assert_grad_parity(got, want, rows, where=f"edge mode={mode}")
+        _, Vr = oracle.black_price(F, K, T, np.where(np.isfinite(ref), ref, 1.0), flag)
+        assert_grad_parity(got, want, np.ones(len(F), bool), where=f"edge mode={mode}", vega=Vr)
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 33, 255, 257, 4097])
