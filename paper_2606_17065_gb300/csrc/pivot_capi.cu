@@ -31,21 +31,6 @@ __global__ void __launch_bounds__(kBlock) k_black_price(int64_t n, const double*
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_iv_forward(int64_t n, const double* __restrict__ F,
-                                                       const double* __restrict__ K, const double* __restrict__ T,
-                                                       const double* __restrict__ P, const int8_t* __restrict__ flag,
-                                                       double* __restrict__ sigma, uint8_t* __restrict__ status,
-                                                       int steps) {
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const pivot::Prepared p = pivot::prepare(F[i], K[i], T[i], P[i], flag[i]);
-    double sig = p.sigma;
-    if (p.status == 0) sig = pivot::solve_s(p, steps, nullptr) / p.sqrtT;
-    sigma[i] = sig;
-    if (status) status[i] = uint8_t(p.status);
-  }
-}
-
 __global__ void __launch_bounds__(kBlock) k_iv_backward(int64_t n, const double* __restrict__ F,
                                                         const double* __restrict__ K, const double* __restrict__ T,
                                                         const int8_t* __restrict__ flag,
@@ -64,26 +49,141 @@ __global__ void __launch_bounds__(kBlock) k_iv_backward(int64_t n, const double*
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_iv_forward_backward(
-    int64_t n, const double* __restrict__ F, const double* __restrict__ K, const double* __restrict__ T,
-    const double* __restrict__ P, const int8_t* __restrict__ flag, const double* __restrict__ gbar, double tau,
-    int mode, double* __restrict__ sigma, uint8_t* __restrict__ status, double* __restrict__ dP,
-    double* __restrict__ dF, double* __restrict__ dK, double* __restrict__ dT, int steps) {
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const double f = F[i], k = K[i], tt = T[i];
-    const int fl = flag[i];
-    const pivot::Prepared p = pivot::prepare(f, k, tt, P[i], fl);
-    double sig = p.sigma;
-    if (p.status == 0) sig = pivot::solve_s(p, steps, nullptr) / p.sqrtT;
-    sigma[i] = sig;
-    if (status) status[i] = uint8_t(p.status);
-    const double g = gbar ? gbar[i] : 1.0;
-    const pivot::Grad d = pivot::gated_adjoint(f, k, tt, fl, sig, g, tau, mode);
-    if (dP) dP[i] = d.dP;
-    if (dF) dF[i] = d.dF;
-    if (dK) dK[i] = d.dK;
-    if (dT) dT[i] = d.dT;
+// ---------------------------------------------------------------------------
+// Forward (and fused forward+backward) with per-tile compaction and region
+// binning.  A block owns a tile of kTile consecutive rows.
+//  phase 1: every thread classifies kTile/kBlock rows (coalesced loads):
+//           rows that need no solve (status != 0: invalid, at a bound) are
+//           finished at once; the others get their LBR boundary node and
+//           region, kept in shared memory, and are counted per region with
+//           one warp-aggregated atomic per (warp, region, row slot).
+//  phase 2: the solved rows are laid out region after region and consumed
+//           in that order, so a warp runs one region's guess and Householder
+//           objective with all of its lanes; only the warps that straddle a
+//           region boundary diverge.
+// The grid is persistent: blocks stride over tiles.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 1024;
+constexpr int kRowsPerThread = kTile / kBlock;
+constexpr int kNodeFields = 6;
+constexpr size_t kBinnedSmem = size_t(kNodeFields) * kTile * sizeof(double) + kTile * sizeof(uint16_t);
+
+struct Args {
+  int64_t n;
+  const double *F, *K, *T, *P;
+  const int8_t* flag;
+  const double* gbar;
+  double tau;
+  int mode;
+  int steps;
+  double* sigma;
+  uint8_t* status;
+  double *dP, *dF, *dK, *dT;
+};
+
+__device__ __forceinline__ void write_grad(const Args& a, int64_t i, double F, double K, double T, int fl,
+                                           double sig) {
+  const double g = a.gbar ? a.gbar[i] : 1.0;
+  const pivot::Grad d = pivot::gated_adjoint(F, K, T, fl, sig, g, a.tau, a.mode);
+  if (a.dP) a.dP[i] = d.dP;
+  if (a.dF) a.dF[i] = d.dF;
+  if (a.dK) a.dK[i] = d.dK;
+  if (a.dT) a.dT[i] = d.dT;
+}
+
+template <bool kBackward>
+__global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
+  extern __shared__ double smem[];
+  double* s_x = smem;
+  double* s_bmax = s_x + kTile;
+  double* s_e = s_bmax + kTile;
+  double* s_bn = s_e + kTile;
+  double* s_bsn = s_bn + kTile;
+  double* s_bb = s_bsn + kTile;
+  uint16_t* s_order = reinterpret_cast<uint16_t*>(s_bb + kTile);
+  __shared__ int s_cnt[4];
+  __shared__ int s_off[5];
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int64_t base = int64_t(blockIdx.x) * kTile; base < a.n; base += int64_t(gridDim.x) * kTile) {
+    if (tid < 4) s_cnt[tid] = 0;
+    __syncthreads();
+    int reg[kRowsPerThread], pos[kRowsPerThread];
+#pragma unroll
+    for (int j = 0; j < kRowsPerThread; ++j) {
+      const int r = j * kBlock + tid;
+      const int64_t i = base + r;
+      int rg = -1;
+      if (i < a.n) {
+        const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
+        const int fl = a.flag[i];
+        const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
+        if (q.status != 0) {
+          a.sigma[i] = q.sigma;
+          if (a.status) a.status[i] = uint8_t(q.status);
+          if (kBackward) write_grad(a, i, F, K, T, fl, q.sigma);
+        } else {
+          double x, bmax;
+          pivot::moneyness(F, K, x, bmax);
+          const double rsq = rsqrt(F * K);
+          pivot::Node nd;
+          rg = pivot::classify(x, bmax, q.tv * rsq, q.cv * rsq, nd);
+          s_x[r] = nd.x;
+          s_bmax[r] = nd.bmax;
+          s_e[r] = nd.e;
+          s_bn[r] = nd.bn;
+          s_bsn[r] = nd.bsn;
+          s_bb[r] = nd.bb;
+        }
+      }
+      reg[j] = rg;
+      pos[j] = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const unsigned m = __ballot_sync(0xffffffffu, rg == k);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          int b0 = 0;
+          if (lane == leader) b0 = atomicAdd(&s_cnt[k], __popc(m));
+          b0 = __shfl_sync(0xffffffffu, b0, leader);
+          if (rg == k) pos[j] = b0 + __popc(m & lt_mask);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_off[0] = 0;
+      for (int k = 0; k < 4; ++k) s_off[k + 1] = s_off[k] + s_cnt[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kRowsPerThread; ++j)
+      if (reg[j] >= 0) s_order[s_off[reg[j]] + pos[j]] = uint16_t(j * kBlock + tid);
+    __syncthreads();
+    const int total = s_off[4];
+    for (int qi = tid; qi < total; qi += kBlock) {
+      const int r = s_order[qi];
+      const int rg = (qi >= s_off[3]) ? 3 : (qi >= s_off[2]) ? 2 : (qi >= s_off[1]) ? 1 : 0;
+      const int64_t i = base + r;
+      pivot::Node nd;
+      nd.x = s_x[r];
+      nd.bmax = s_bmax[r];
+      nd.e = s_e[r];
+      nd.bn = s_bn[r];
+      nd.bsn = s_bsn[r];
+      nd.bb = s_bb[r];
+      const double F = a.F[i], K = a.K[i], T = a.T[i];
+      const int fl = a.flag[i];
+      const double lnbeta = (rg == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, a.P[i], fl) : 0.0;
+      const double s = pivot::solve_region(rg, nd, lnbeta, a.steps);
+      const double sig = s / sqrt(T);
+      a.sigma[i] = sig;
+      if (a.status) a.status[i] = 0;
+      if (kBackward) write_grad(a, i, F, K, T, fl, sig);
+    }
+    __syncthreads();
   }
 }
 
@@ -156,6 +256,31 @@ int select_device(int device) {
   return PIVOT_OK;
 }
 
+// persistent grid for the binned kernels: resident blocks x SMs, capped by the tiles
+template <bool kBackward>
+int launch_binned(const Args& a, void* stream) {
+  static thread_local int configured_device = -1;
+  static thread_local int blocks_per_sm = 0, num_sms = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
+  if (configured_device != dev) {
+    cudaFuncSetAttribute(k_iv_binned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBinnedSmem));
+    cudaFuncSetAttribute(k_iv_binned<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBinnedSmem));
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    int b0 = 0, b1 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_iv_binned<false>, kBlock, kBinnedSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_iv_binned<true>, kBlock, kBinnedSmem);
+    blocks_per_sm = b0 < b1 ? b0 : b1;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    configured_device = dev;
+  }
+  const int64_t tiles = (a.n + kTile - 1) / kTile;
+  const int64_t cap = int64_t(blocks_per_sm) * num_sms;
+  const unsigned grid = unsigned(tiles < cap ? tiles : cap);
+  k_iv_binned<kBackward><<<grid, kBlock, kBinnedSmem, static_cast<cudaStream_t>(stream)>>>(a);
+  return launch_status();
+}
+
 }  // namespace
 
 extern "C" {
@@ -190,9 +315,8 @@ int pivot_iv_forward(int64_t n, const double* F, const double* K, const double* 
   rc = check_all(ps, &dev);
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
-  k_iv_forward<<<grid_for(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(n, F, K, T, P, flag, sigma_out,
-                                                                                 status_out, steps);
-  return launch_status();
+  Args a{n, F, K, T, P, flag, nullptr, 0.0, 0, steps, sigma_out, status_out, nullptr, nullptr, nullptr, nullptr};
+  return launch_binned<false>(a, stream);
 }
 
 int pivot_iv_backward(int64_t n, const double* F, const double* K, const double* T, const int8_t* flag,
@@ -232,9 +356,8 @@ int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const
   rc = check_all(ps, &dev);
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
-  k_iv_forward_backward<<<grid_for(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(
-      n, F, K, T, P, flag, gbar, tau, gate_mode, sigma_out, status_out, dP, dF, dK, dT, steps);
-  return launch_status();
+  Args a{n, F, K, T, P, flag, gbar, tau, gate_mode, steps, sigma_out, status_out, dP, dF, dK, dT};
+  return launch_binned<true>(a, stream);
 }
 
 const char* pivot_error_string(int code) {

@@ -37,8 +37,11 @@ constexpr double kLn2 = 0.693147180559945309417;
 
 // Taylor zone of rho: t <= kTaylorT and |x| <= kTaylorX; 9 odd terms reach
 // double precision for t <= 0.25 at every h <= 0 (c_n(h) <= c_n(0)).
+// Outside it the difference Y(h + t) - Y(h - t) is used: its rounding moves
+// sigma by about eps Y(h + t) / s <= eps / |x| in relative terms, at most
+// 10 eps for |x| >= 0.1, and by <= 1.25 eps / s <= 2.5 eps for t > 0.25.
 constexpr double kTaylorT = 0.25;
-constexpr double kTaylorX = 2.0;
+constexpr double kTaylorX = 0.1;
 
 enum Region : int { kLower = 0, kMidLow = 1, kMidHigh = 2, kUpper = 3 };
 
@@ -114,17 +117,6 @@ __device__ __forceinline__ double shape_monotone(double D, double y0, double y1,
 // Row preparation (Algorithm 1 forward normalisation with r = 0; appendix
 // stages 1-2).
 // ---------------------------------------------------------------------------
-struct Prepared {
-  double x;      // -|ln(F/K)|
-  double bmax;   // e^{x/2}
-  double beta;   // tv / sqrt(FK)
-  double betac;  // (U - P) / sqrt(FK) = b_max - beta, without cancellation
-  double lnbeta; // ln beta, finite even where beta is subnormal
-  double sqrtT;
-  int status;    // PIVOT_ROW_* ; 0 means "solve"
-  double sigma;  // result for rows that need no solve
-};
-
 __device__ __forceinline__ bool bad_inputs(double F, double K, double T, int flag) {
   // also rejects NaN and +-inf
   return !(F > 0.0 && F < INFINITY) || !(K > 0.0 && K < INFINITY) || !(T > 0.0 && T < INFINITY) ||
@@ -156,31 +148,44 @@ __device__ __forceinline__ void moneyness(double F, double K, double& x, double&
   bmax = sqrt(mn / mx);
 }
 
-__device__ __forceinline__ Prepared prepare(double F, double K, double T, double P, int flag) {
-  Prepared r;
-  r.status = 0;
-  r.sigma = 0.0;
+// Stage 1 for one quote: validity, the time value tv = P - intrinsic (exact
+// up to one rounding) and cv = U - P (U = F for calls, K for puts).  Rows that
+// need no solve get their status and sigma here (Section 3.1: invalid rows
+// are NaN; PIVOT_ROW_* codes).
+struct Quote {
+  double tv, cv;
+  int status;   // 0: solve
+  double sigma; // result when status != 0
+};
+
+__device__ __forceinline__ Quote classify_quote(double F, double K, double T, double P, int flag) {
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  Quote q;
+  q.tv = q.cv = 0.0;
+  q.status = 0;
+  q.sigma = 0.0;
   if (bad_inputs(F, K, T, flag) || !(fabs(P) < INFINITY)) {
-    r.status = 3;
-    r.sigma = __longlong_as_double(0x7ff8000000000000LL);
-    return r;
+    q.status = 3;
+    q.sigma = qnan;
+    return q;
   }
   const bool call = flag > 0;
   const bool itm = call ? (F > K) : (K > F);
-  const double tv = itm ? (call ? time_value_itm(P, F, K) : time_value_itm(P, K, F)) : P;
-  const double cv = (call ? F : K) - P;
-  if (tv < 0.0) { r.status = 1; r.sigma = __longlong_as_double(0x7ff8000000000000LL); return r; }
-  if (cv < 0.0) { r.status = 2; r.sigma = __longlong_as_double(0x7ff8000000000000LL); return r; }
-  if (tv == 0.0) { r.status = 4; r.sigma = 0.0; return r; }
-  if (cv == 0.0) { r.status = 5; r.sigma = INFINITY; return r; }
-  moneyness(F, K, r.x, r.bmax);
-  const double rsq = rsqrt(F * K);
-  r.beta = tv * rsq;
-  r.betac = cv * rsq;
-  // beta near or below the subnormal range: take ln beta from ln tv
-  r.lnbeta = (r.beta > 1e-290) ? log(r.beta) : log(tv) + log(rsq);
-  r.sqrtT = sqrt(T);
-  return r;
+  q.tv = itm ? (call ? time_value_itm(P, F, K) : time_value_itm(P, K, F)) : P;
+  q.cv = (call ? F : K) - P;
+  if (q.tv < 0.0) { q.status = 1; q.sigma = qnan; }
+  else if (q.cv < 0.0) { q.status = 2; q.sigma = qnan; }
+  else if (q.tv == 0.0) { q.status = 4; q.sigma = 0.0; }
+  else if (q.cv == 0.0) { q.status = 5; q.sigma = INFINITY; }
+  return q;
+}
+
+// ln beta for a solved row; beta near or below the subnormal range takes it
+// from ln tv so that it keeps its relative accuracy
+__device__ __forceinline__ double log_beta(double beta, double F, double K, double T, double P, int flag) {
+  if (beta > 1e-290) return log(beta);
+  const Quote q = classify_quote(F, K, T, P, flag);
+  return log(q.tv) + log(rsqrt(F * K));
 }
 
 // ---------------------------------------------------------------------------
@@ -190,76 +195,105 @@ __device__ __forceinline__ Prepared prepare(double F, double K, double T, double
 // form, with e = erfcx(sqrt|x|):
 //   b_c = b_max (1 - e)/2,  b_s(s_c) = b_max/sqrt(2 pi),
 //   s_l = s_c - sqrt(pi/2)(1 - e),  s_u = s_c + sqrt(pi/2)(1 + e).
+// Only one of b_l = b(s_l), b_u = b(s_u) is needed per row (the side of b_c
+// that beta is on); both cost two erfcx and one exp and are evaluated by the
+// same branch-free code: b_l = b_s (Y(h + t) - Y(h - t)) and
+// b_max - b_u = b_s (Y(-h - t) + Y(h - t)).  The node only seeds the guess,
+// so the difference form is accurate enough for it everywhere.
 // ---------------------------------------------------------------------------
-struct Guess {
-  double s;
-  int region;
+struct Node {
+  double x;    // -|ln(F/K)|
+  double bmax; // e^{x/2}
+  double e;    // erfcx(sqrt|x|)
+  double bn;   // b_l (lower side) or b_max - b_u (upper side)
+  double bsn;  // b_s at that node
+  double bb;   // beta, or beta_c = b_max - beta in the upper region
 };
 
-__device__ __forceinline__ Guess initial_guess(const Prepared& p) {
-  const double x = p.x, ax = -x;
+__device__ __forceinline__ int classify(double x, double bmax, double beta, double betac, Node& nd) {
+  const double ax = -x;
   const double sc = sqrt(2.0 * ax);
   const double e = erfcx(sc * kInvSqrt2);
-  const double bc = 0.5 * p.bmax * (1.0 - e);
-  const double dc = kSqrt2Pi / p.bmax; // ds/db at s_c
-  Guess g;
-  if (p.beta <= bc) {
-    const double sl = sc - kSqrtPiOver2 * (1.0 - e);
-    double bl = 0.0, bsl = 1.0;
-    if (sl > 0.0) {
-      const double hl = x / sl, tl = 0.5 * sl;
-      bsl = exp(log_bs(hl, tl));
-      bl = bsl * rho_of(x, hl, tl);
-    }
-    if (p.beta >= bl) {
-      // middle, lower half: rational cubic in b on [b_l, b_c], s''(b_c) = 0
-      const double D = bc - bl;
-      const double d0 = 1.0 / bsl;
-      const double r = shape_zero_curv_right(D, sl, sc, d0, dc);
-      g.s = rational_cubic(p.beta, bl, bc, sl, sc, d0, dc, r);
-      g.region = kMidLow;
-    } else {
-      // lower tail: b ~ kappa Phi(-|x|/(sqrt3 s))^3 as s -> 0 with
-      // kappa = 2 pi |x| / (3 sqrt 3).  Interpolate G = Phi(-|x|/(sqrt3 s))
-      // against u = (beta/kappa)^(1/3) on [0, u_l]: G(0) = 0, G'(0) = 1,
-      // G(u_l), G'(u_l) exact; then invert G for s.
+  const double bc = 0.5 * bmax * (1.0 - e);
+  const bool low = beta <= bc;
+  const double sl = sc - kSqrtPiOver2 * (1.0 - e);
+  const double su = sc + kSqrtPiOver2 * (1.0 + e);
+  const bool has_l = sl > 0.0;
+  const double sn = low ? (has_l ? sl : 1.0) : su;
+  const double h = x / sn, t = 0.5 * sn;
+  const double y1 = mills_y(low ? h + t : -h - t);
+  const double y2 = mills_y(h - t);
+  const double bs = exp(log_bs(h, t));
+  const double val = bs * (low ? y1 - y2 : y1 + y2);
+  nd.x = x;
+  nd.bmax = bmax;
+  nd.e = e;
+  nd.bn = (low && !has_l) ? 0.0 : val;
+  nd.bsn = bs;
+  int region;
+  if (low) region = (beta < nd.bn) ? kLower : kMidLow;
+  else region = (beta <= bmax - val) ? kMidHigh : kUpper;
+  nd.bb = (region == kUpper) ? betac : beta;
+  return region;
+}
+
+// Rational initial guess s^(0) of the row's region from its node.
+// lnbeta is ln beta (lower region only).
+__device__ __forceinline__ double region_guess(int region, const Node& nd, double lnbeta) {
+  const double x = nd.x, ax = -x;
+  const double sc = sqrt(2.0 * ax);
+  const double e = nd.e;
+  const double dc = kSqrt2Pi / nd.bmax; // ds/db at s_c
+  switch (region) {
+    case kLower: {
+      // lower tail: b ~ kappa Phi(-|x|/(sqrt3 s))^3 as s -> 0, kappa = 2 pi |x| / (3 sqrt 3).
+      // Interpolate G = Phi(-|x|/(sqrt3 s)) against u = (beta/kappa)^(1/3) on [0, u_l]
+      // (G(0) = 0, G'(0) = 1, G(u_l), G'(u_l) exact), then invert G for s.
+      const double sl = sc - kSqrtPiOver2 * (1.0 - e);
+      const double bl = nd.bn, bsl = nd.bsn, beta = nd.bb;
       const double kap = kTwoPiOver3Sqrt3 * ax;
-      const double u = (p.beta > 1e-280) ? cbrt(p.beta / kap) : exp((p.lnbeta - log(kap)) * (1.0 / 3.0));
+      const double u = (beta > 1e-280) ? cbrt(beta / kap) : exp((lnbeta - log(kap)) * (1.0 / 3.0));
       const double ul = cbrt(bl / kap);
       const double al = ax * kInvSqrt3 / sl;
       const double Gl = normcdf(-al);
       const double dGl = 3.0 * bl * (kInvSqrt2Pi * exp(-0.5 * al * al)) * al / (sl * ul * bsl);
       const double r = shape_monotone(ul, 0.0, Gl, 1.0, dGl);
       const double G = fmin(rational_cubic(u, 0.0, ul, 0.0, Gl, 1.0, dGl, r), 0.5);
-      g.s = ax * kInvSqrt3 / (-normcdfinv(G));
-      g.region = kLower;
+      return ax * kInvSqrt3 / (-normcdfinv(G));
     }
-  } else {
-    const double su = sc + kSqrtPiOver2 * (1.0 + e);
-    const double hu = x / su, tu = 0.5 * su;
-    const double bsu = exp(log_bs(hu, tu));
-    const double cu = bsu * gamma_of(hu, tu);
-    const double bu = p.bmax - cu;
-    if (p.beta <= bu) {
-      // middle, upper half: rational cubic in b on [b_c, b_u], s''(b_c) = 0
+    case kMidLow: {
+      // rational cubic in b on [b_l, b_c], zero curvature of s(b) at the inflection b_c
+      const double sl = sc - kSqrtPiOver2 * (1.0 - e);
+      const double bc = 0.5 * nd.bmax * (1.0 - e);
+      const double bl = nd.bn;
+      const double d0 = (bl > 0.0) ? 1.0 / nd.bsn : dc;
+      const double s0 = (bl > 0.0) ? sl : 0.0;
+      const double D = bc - bl;
+      const double r = shape_zero_curv_right(D, s0, sc, d0, dc);
+      return rational_cubic(nd.bb, bl, bc, s0, sc, d0, dc, r);
+    }
+    case kMidHigh: {
+      // rational cubic in b on [b_c, b_u], zero curvature of s(b) at b_c
+      const double su = sc + kSqrtPiOver2 * (1.0 + e);
+      const double bc = 0.5 * nd.bmax * (1.0 - e);
+      const double bu = nd.bmax - nd.bn;
+      const double d1 = 1.0 / nd.bsn;
       const double D = bu - bc;
-      const double d1 = 1.0 / bsu;
       const double r = shape_zero_curv_left(D, sc, su, dc, d1);
-      g.s = rational_cubic(p.beta, bc, bu, sc, su, dc, d1, r);
-      g.region = kMidHigh;
-    } else {
+      return rational_cubic(nd.bb, bc, bu, sc, su, dc, d1, r);
+    }
+    default: {
       // upper tail: b_max - b ~ 2 Phi(-s/2) as s -> inf.  Interpolate
       // v = Phi(-s/2) against u = (b_max - beta)/2 on [0, u_u], v'(0) = 1.
-      const double uu = 0.5 * cu;
+      const double su = sc + kSqrtPiOver2 * (1.0 + e);
+      const double uu = 0.5 * nd.bn;
       const double vu = normcdf(-0.5 * su);
-      const double dvu = (kInvSqrt2Pi * exp(-0.125 * su * su)) / bsu;
+      const double dvu = (kInvSqrt2Pi * exp(-0.125 * su * su)) / nd.bsn;
       const double r = shape_monotone(uu, 0.0, vu, 1.0, dvu);
-      const double v = fmin(rational_cubic(0.5 * p.betac, 0.0, uu, 0.0, vu, 1.0, dvu, r), 0.5);
-      g.s = -2.0 * normcdfinv(v);
-      g.region = kUpper;
+      const double v = fmin(rational_cubic(0.5 * nd.bb, 0.0, uu, 0.0, vu, 1.0, dvu, r), 0.5);
+      return -2.0 * normcdfinv(v);
     }
   }
-  return g;
 }
 
 // ---------------------------------------------------------------------------
@@ -271,9 +305,8 @@ __device__ __forceinline__ Guess initial_guess(const Prepared& p) {
 //   s <- s + nu (1 + h2 nu / 2) / (1 + nu (h2 + h3 nu / 6)),
 //   nu = -f/f', h2 = f''/f', h3 = f'''/f'.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double householder_step(const Prepared& p, double lnbetac, double inv_lnbeta,
+__device__ __forceinline__ double householder_step(double x, double beta, double lnbetac, double inv_lnbeta,
                                                    int region, double s) {
-  const double x = p.x;
   const double inv_s = 1.0 / s;
   const double h = x * inv_s, t = 0.5 * s;
   const double hh = h * h;
@@ -299,7 +332,7 @@ __device__ __forceinline__ double householder_step(const Prepared& p, double lnb
   } else {
     const double rho = rho_of(x, h, t);
     const double bs = exp(log_bs(h, t));
-    nu = p.beta / bs - rho; // (beta - b)/b'
+    nu = beta / bs - rho; // (beta - b)/b'
     h2 = b2;
     h3 = b3;
   }
@@ -308,14 +341,12 @@ __device__ __forceinline__ double householder_step(const Prepared& p, double lnb
   return s + num / den;
 }
 
-// Forward solve for a prepared row with status 0; returns s.
-__device__ __forceinline__ double solve_s(const Prepared& p, int steps, int* region_out) {
-  Guess g = initial_guess(p);
-  const double lnbetac = (g.region == kUpper) ? log(p.betac) : 0.0;
-  const double inv_lnbeta = (g.region == kLower) ? 1.0 / p.lnbeta : 0.0;
-  double s = g.s;
-  for (int i = 0; i < steps; ++i) s = householder_step(p, lnbetac, inv_lnbeta, g.region, s);
-  if (region_out) *region_out = g.region;
+// Guess plus `steps` Householder(3) steps for a classified row; returns s.
+__device__ __forceinline__ double solve_region(int region, const Node& nd, double lnbeta, int steps) {
+  const double lnbetac = (region == kUpper) ? log(nd.bb) : 0.0;
+  const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
+  double s = region_guess(region, nd, lnbeta);
+  for (int i = 0; i < steps; ++i) s = householder_step(nd.x, nd.bb, lnbetac, inv_lnbeta, region, s);
   return s;
 }
 
@@ -358,14 +389,10 @@ __device__ __forceinline__ Grad gated_adjoint(double F, double K, double T, int 
   const double h = xs * inv_s, t = 0.5 * s;
   const double V = sqrt(F * K) * sqT * exp(log_bs(h, t));
   const double d1 = h + t, d2 = h - t;
-  double jF, jK;
-  if (flag > 0) {
-    jF = -mills_y(d1) / (F * sqT);
-    jK = mills_y(d2) / (K * sqT);
-  } else {
-    jF = mills_y(-d1) / (F * sqT);
-    jK = -mills_y(-d2) / (K * sqT);
-  }
+  // call: jF = -Y(d1)/(F sqrt T), jK = Y(d2)/(K sqrt T); put: the same of -d1, -d2 with signs flipped
+  const double sg = flag > 0 ? 1.0 : -1.0;
+  const double jF = -sg * mills_y(sg * d1) / (F * sqT);
+  const double jK = sg * mills_y(sg * d2) / (K * sqT);
   const double jT = -sigma / (2.0 * T);
   const bool in_g = fabs(V) > tau;
   if (mode == 0 || (mode <= 2 && in_g)) {
