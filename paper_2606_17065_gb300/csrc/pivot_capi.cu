@@ -52,21 +52,22 @@ __global__ void __launch_bounds__(kBlock) k_iv_backward(int64_t n, const double*
 // ---------------------------------------------------------------------------
 // Forward (and fused forward+backward) with per-tile compaction and region
 // binning.  A block owns a tile of kTile consecutive rows.
-//  phase 1: every thread classifies kTile/kBlock rows (coalesced loads):
-//           rows that need no solve (status != 0: invalid, at a bound) are
-//           finished at once; the others get their LBR boundary node and
-//           region, kept in shared memory, and are counted per region with
-//           one warp-aggregated atomic per (warp, region, row slot).
-//  phase 2: the solved rows are laid out region after region and consumed
-//           in that order, so a warp runs one region's guess and Householder
-//           objective with all of its lanes; only the warps that straddle a
-//           region boundary diverge.
+//  phase 1: every thread classifies kTile/kBlock rows (coalesced loads) with
+//           the cheap stage-1 tests; rows that need no solve (invalid, or at
+//           a bound of the price interval) are finished at once, the others
+//           are appended to a tile-local list (one warp-aggregated atomic).
+//  phase 2: the list is consumed densely: normalisation, LBR boundary node
+//           and region of each row, kept in shared memory, counted per region.
+//  phase 3: the rows are laid out region after region and consumed in that
+//           order, so a warp runs one region's guess and Householder
+//           objective with all of its lanes; only warps straddling a region
+//           boundary diverge.  sigma and the gated adjoint are written here.
 // The grid is persistent: blocks stride over tiles.
 // ---------------------------------------------------------------------------
 constexpr int kTile = 1024;
 constexpr int kRowsPerThread = kTile / kBlock;
 constexpr int kNodeFields = 6;
-constexpr size_t kBinnedSmem = size_t(kNodeFields) * kTile * sizeof(double) + kTile * sizeof(uint16_t);
+constexpr size_t kBinnedSmem = size_t(kNodeFields) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
 
 struct Args {
   int64_t n;
@@ -91,6 +92,18 @@ __device__ __forceinline__ void write_grad(const Args& a, int64_t i, double F, d
   if (a.dT) a.dT[i] = d.dT;
 }
 
+// warp-aggregated append: returns this lane's slot in a shared counter
+__device__ __forceinline__ int warp_append(bool take, int* counter, int lane) {
+  const unsigned m = __ballot_sync(0xffffffffu, take);
+  int b0 = 0;
+  if (m) {
+    const int leader = __ffs(m) - 1;
+    if (lane == leader) b0 = atomicAdd(counter, __popc(m));
+    b0 = __shfl_sync(0xffffffffu, b0, leader);
+  }
+  return b0 + __popc(m & ((1u << lane) - 1u));
+}
+
 template <bool kBackward>
 __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
   extern __shared__ double smem[];
@@ -100,22 +113,24 @@ __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
   double* s_bn = s_e + kTile;
   double* s_bsn = s_bn + kTile;
   double* s_bb = s_bsn + kTile;
-  uint16_t* s_order = reinterpret_cast<uint16_t*>(s_bb + kTile);
+  uint16_t* s_list = reinterpret_cast<uint16_t*>(s_bb + kTile);  // phase 1 -> 2: rows to solve
+  uint16_t* s_order = s_list + kTile;                             // phase 2 -> 3: region order
+  __shared__ int s_nsolve;
   __shared__ int s_cnt[4];
   __shared__ int s_off[5];
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const unsigned lt_mask = (1u << lane) - 1u;
   for (int64_t base = int64_t(blockIdx.x) * kTile; base < a.n; base += int64_t(gridDim.x) * kTile) {
     if (tid < 4) s_cnt[tid] = 0;
+    if (tid == 0) s_nsolve = 0;
     __syncthreads();
-    int reg[kRowsPerThread], pos[kRowsPerThread];
+    // ---- phase 1
 #pragma unroll
     for (int j = 0; j < kRowsPerThread; ++j) {
       const int r = j * kBlock + tid;
       const int64_t i = base + r;
-      int rg = -1;
+      bool solve = false;
       if (i < a.n) {
         const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
         const int fl = a.flag[i];
@@ -125,31 +140,45 @@ __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
           if (a.status) a.status[i] = uint8_t(q.status);
           if (kBackward) write_grad(a, i, F, K, T, fl, q.sigma);
         } else {
-          double x, bmax;
-          pivot::moneyness(F, K, x, bmax);
-          const double rsq = rsqrt(F * K);
-          pivot::Node nd;
-          rg = pivot::classify(x, bmax, q.tv * rsq, q.cv * rsq, nd);
-          s_x[r] = nd.x;
-          s_bmax[r] = nd.bmax;
-          s_e[r] = nd.e;
-          s_bn[r] = nd.bn;
-          s_bsn[r] = nd.bsn;
-          s_bb[r] = nd.bb;
+          solve = true;
         }
+      }
+      const int slot = warp_append(solve, &s_nsolve, lane);
+      if (solve) s_list[slot] = uint16_t(r);
+    }
+    __syncthreads();
+    // ---- phase 2
+    const int nsolve = s_nsolve;
+    int reg[kRowsPerThread], pos[kRowsPerThread], row[kRowsPerThread];
+#pragma unroll
+    for (int j = 0; j < kRowsPerThread; ++j) {
+      const int qi = j * kBlock + tid;
+      int rg = -1;
+      row[j] = 0;
+      if (qi < nsolve) {
+        const int r = s_list[qi];
+        const int64_t i = base + r;
+        const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
+        const pivot::Quote q = pivot::classify_quote(F, K, T, P, a.flag[i]);
+        double x, bmax;
+        pivot::moneyness(F, K, x, bmax);
+        const double rsq = rsqrt(F * K);
+        pivot::Node nd;
+        rg = pivot::classify(x, bmax, q.tv * rsq, q.cv * rsq, nd);
+        s_x[r] = nd.x;
+        s_bmax[r] = nd.bmax;
+        s_e[r] = nd.e;
+        s_bn[r] = nd.bn;
+        s_bsn[r] = nd.bsn;
+        s_bb[r] = nd.bb;
+        row[j] = r;
       }
       reg[j] = rg;
       pos[j] = 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const unsigned m = __ballot_sync(0xffffffffu, rg == k);
-        if (m) {
-          const int leader = __ffs(m) - 1;
-          int b0 = 0;
-          if (lane == leader) b0 = atomicAdd(&s_cnt[k], __popc(m));
-          b0 = __shfl_sync(0xffffffffu, b0, leader);
-          if (rg == k) pos[j] = b0 + __popc(m & lt_mask);
-        }
+        const int p = warp_append(rg == k, &s_cnt[k], lane);
+        if (rg == k) pos[j] = p;
       }
     }
     __syncthreads();
@@ -160,8 +189,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kRowsPerThread; ++j)
-      if (reg[j] >= 0) s_order[s_off[reg[j]] + pos[j]] = uint16_t(j * kBlock + tid);
+      if (reg[j] >= 0) s_order[s_off[reg[j]] + pos[j]] = uint16_t(row[j]);
     __syncthreads();
+    // ---- phase 3
     const int total = s_off[4];
     for (int qi = tid; qi < total; qi += kBlock) {
       const int r = s_order[qi];

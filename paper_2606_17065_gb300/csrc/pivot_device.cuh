@@ -33,7 +33,6 @@ constexpr double kInvSqrt2 = 0.707106781186547524401;
 constexpr double kLnSqrt2Pi = 0.918938533204672741780;
 constexpr double kInvSqrt3 = 0.577350269189625764509;
 constexpr double kTwoPiOver3Sqrt3 = 1.20919957615614523543; // 2 pi / (3 sqrt 3)
-constexpr double kLn2 = 0.693147180559945309417;
 
 // Taylor zone of rho: t <= kTaylorT and |x| <= kTaylorX; 9 odd terms reach
 // double precision for t <= 0.25 at every h <= 0 (c_n(h) <= c_n(0)).
@@ -45,7 +44,9 @@ constexpr double kTaylorX = 0.1;
 
 enum Region : int { kLower = 0, kMidLow = 1, kMidHigh = 2, kUpper = 3 };
 
-__device__ __forceinline__ double mills_y(double z) { return kSqrtPiOver2 * erfcx(-z * kInvSqrt2); }
+// Y(z) = Phi(z)/phi(z).  Kept out of line: it is called from many sites and
+// one shared copy keeps the kernels' instruction footprint small.
+__device__ __noinline__ double mills_y(double z) { return kSqrtPiOver2 * erfcx(-z * kInvSqrt2); }
 
 // ln b_s(x, s) = -(h^2 + t^2)/2 - ln sqrt(2 pi)
 __device__ __forceinline__ double log_bs(double h, double t) {
@@ -134,18 +135,22 @@ __device__ __forceinline__ double time_value_itm(double P, double a, double b) {
   return s2 + (e1 + e2);
 }
 
-// -|ln(F/K)| from mn = min(F, K), mx = max(F, K): within a factor 2, mx - mn
-// is exact (Sterbenz) and log1p keeps the relative accuracy near the money;
-// further out, the ratio itself is accurate.
-__device__ __forceinline__ double neg_abs_log_ratio(double mn, double mx) {
-  return (mn >= 0.5 * mx) ? log1p(-(mx - mn) / mx) : log(mn / mx);
+// -|ln(F/K)| from mn = min(F, K), mx = max(F, K), branch-free and accurate
+// near the money: r = mn/mx is correctly rounded, so its residual
+// c = (mn - r mx)/mn is exact to first order (one fma) and
+// ln(mn/mx) = ln r + ln(1 + c) = ln r + c + O(c^2), |c| <= 2^-53.
+__device__ __forceinline__ double neg_abs_log_ratio(double mn, double mx, double* ratio = nullptr) {
+  const double r = mn / mx;
+  const double c = fma(-r, mx, mn) / mn;
+  if (ratio) *ratio = r;
+  return log(r) + c;
 }
 
 // x = -|ln(F/K)|, b_max = e^{x/2} = sqrt(min/max)
 __device__ __forceinline__ void moneyness(double F, double K, double& x, double& bmax) {
-  const double mn = fmin(F, K), mx = fmax(F, K);
-  x = neg_abs_log_ratio(mn, mx);
-  bmax = sqrt(mn / mx);
+  double r;
+  x = neg_abs_log_ratio(fmin(F, K), fmax(F, K), &r);
+  bmax = sqrt(r);
 }
 
 // Stage 1 for one quote: validity, the time value tv = P - intrinsic (exact
