@@ -40,11 +40,13 @@ WORKLOAD = ("stress-16M: ln(K/F)~U[-6,6], sigma*sqrt(T) log-uniform [1e-4,3], T~
 # in; sigma (8) + status (1) + dP, dF, dK, dT (4 x 8) out.
 BYTES_PER_ROW = 33 + 41
 # FP64 FLOPs per row of the fused kernel on this workload, counted by ncu
-# (smsp__sass_thread_inst_executed_op_{dadd,dmul}_pred_on + 2 x ..._dfma_pred_on,
-# summed over one launch, divided by the rows); see profiles/.  None until counted.
-FLOPS_PER_ROW = None
-# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), None until captured.
-TRAFFIC_PER_ROW = None
+# (smsp__sass_thread_inst_executed_op_{dadd,dmul}_pred_on + 2 x ..._dfma_pred_on
+# over one launch of 4,194,304 stress rows, divided by the rows), see
+# profiles/k_iv_binned_fwdbwd_stress.md.  Counts scale with the rows: every
+# launch of the same distribution does the same work per row on average.
+FLOPS_PER_ROW = 781.1
+# dram__bytes_read.sum + dram__bytes_write.sum per row from the same capture.
+TRAFFIC_PER_ROW = (210.280448e6 + 187.428864e6) / 4194304
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA lanes/clk x 2 FLOP
 # (= 1.25 TFLOP/s nominal at 2.07 GHz), scaled by the SM clock seen under load.
 SMS = 152
