@@ -145,6 +145,11 @@ def dist_setup(args):
     return rank, world
 
 
+def shard_seed(rank: int) -> int:
+    """Each rank draws its own independent rows (weak scaling): seed 2 + rank."""
+    return 2 + rank
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -221,7 +226,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
 
     # inputs: this rank's own shard of independent rows (weak scaling)
-    b = workloads.stress_batch(args.rows, seed=2 + rank)
+    b = workloads.stress_batch(args.rows, seed=shard_seed(rank))
     n = b.n
     F = torch.from_numpy(b.F).to(dev)
     K = torch.from_numpy(b.K).to(dev)
