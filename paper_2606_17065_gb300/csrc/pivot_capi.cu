@@ -67,6 +67,12 @@ __global__ void __launch_bounds__(kBlock) k_iv_backward(int64_t n, const double*
 constexpr int kTile = 1024;
 constexpr int kRowsPerThread = kTile / kBlock;
 constexpr int kNodeFields = 6;
+// mixed mode: 4 float-seeded region bins plus 4 FP64 bins for rows outside
+// the float range (beta or b_max - beta below kMixedFloor, or |x| above
+// kMixedMaxAbsX, where the float node would underflow)
+constexpr int kBins = 8;
+constexpr double kMixedFloor = 1e-30;
+constexpr double kMixedMaxAbsX = 80.0;
 constexpr size_t kBinnedSmem = size_t(kNodeFields) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
 
 struct Args {
@@ -104,7 +110,7 @@ __device__ __forceinline__ int warp_append(bool take, int* counter, int lane) {
   return b0 + __popc(m & ((1u << lane) - 1u));
 }
 
-template <bool kBackward>
+template <bool kBackward, bool kMixed>
 __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
   extern __shared__ double smem[];
   double* s_x = smem;
@@ -116,13 +122,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
   uint16_t* s_list = reinterpret_cast<uint16_t*>(s_bb + kTile);  // phase 1 -> 2: rows to solve
   uint16_t* s_order = s_list + kTile;                             // phase 2 -> 3: region order
   __shared__ int s_nsolve;
-  __shared__ int s_cnt[4];
-  __shared__ int s_off[5];
+  __shared__ int s_cnt[kBins];
+  __shared__ int s_off[kBins + 1];
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   for (int64_t base = int64_t(blockIdx.x) * kTile; base < a.n; base += int64_t(gridDim.x) * kTile) {
-    if (tid < 4) s_cnt[tid] = 0;
+    if (tid < kBins) s_cnt[tid] = 0;
     if (tid == 0) s_nsolve = 0;
     __syncthreads();
     // ---- phase 1
@@ -163,20 +169,38 @@ __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
         double x, bmax;
         pivot::moneyness(F, K, x, bmax);
         const double rsq = rsqrt(F * K);
-        pivot::Node nd;
-        rg = pivot::classify(x, bmax, q.tv * rsq, q.cv * rsq, nd);
-        s_x[r] = nd.x;
-        s_bmax[r] = nd.bmax;
-        s_e[r] = nd.e;
-        s_bn[r] = nd.bn;
-        s_bsn[r] = nd.bsn;
-        s_bb[r] = nd.bb;
+        const double beta = q.tv * rsq, betac = q.cv * rsq;
+        bool fp64_row = true;
+        if (kMixed && beta > kMixedFloor && betac > kMixedFloor && x > -kMixedMaxAbsX) {
+          // float node and region; the float copies are exact in double storage
+          pivot::Node<float> nf;
+          rg = pivot::classify<float>(float(x), float(bmax), float(beta), float(betac), nf);
+          if (nf.bsn > 0.0f && nf.bn >= 0.0f) {
+            fp64_row = false;
+            s_x[r] = x;
+            s_bmax[r] = double(nf.bmax);
+            s_e[r] = double(nf.e);
+            s_bn[r] = double(nf.bn);
+            s_bsn[r] = double(nf.bsn);
+            s_bb[r] = (rg == pivot::kUpper) ? betac : beta;
+          }
+        }
+        if (fp64_row) {
+          pivot::Node<double> nd;
+          rg = pivot::classify<double>(x, bmax, beta, betac, nd) + (kMixed ? 4 : 0);
+          s_x[r] = nd.x;
+          s_bmax[r] = nd.bmax;
+          s_e[r] = nd.e;
+          s_bn[r] = nd.bn;
+          s_bsn[r] = nd.bsn;
+          s_bb[r] = nd.bb;
+        }
         row[j] = r;
       }
       reg[j] = rg;
       pos[j] = 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < kBins; ++k) {
         const int p = warp_append(rg == k, &s_cnt[k], lane);
         if (rg == k) pos[j] = p;
       }
@@ -184,7 +208,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
     __syncthreads();
     if (tid == 0) {
       s_off[0] = 0;
-      for (int k = 0; k < 4; ++k) s_off[k + 1] = s_off[k] + s_cnt[k];
+      for (int k = 0; k < kBins; ++k) s_off[k + 1] = s_off[k] + s_cnt[k];
     }
     __syncthreads();
 #pragma unroll
@@ -192,22 +216,49 @@ __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
       if (reg[j] >= 0) s_order[s_off[reg[j]] + pos[j]] = uint16_t(row[j]);
     __syncthreads();
     // ---- phase 3
-    const int total = s_off[4];
+    const int total = s_off[kBins];
     for (int qi = tid; qi < total; qi += kBlock) {
       const int r = s_order[qi];
-      const int rg = (qi >= s_off[3]) ? 3 : (qi >= s_off[2]) ? 2 : (qi >= s_off[1]) ? 1 : 0;
+      int bin = 0;
+#pragma unroll
+      for (int k = 1; k < kBins; ++k) bin += (qi >= s_off[k]) ? 1 : 0;
       const int64_t i = base + r;
-      pivot::Node nd;
-      nd.x = s_x[r];
-      nd.bmax = s_bmax[r];
-      nd.e = s_e[r];
-      nd.bn = s_bn[r];
-      nd.bsn = s_bsn[r];
-      nd.bb = s_bb[r];
       const double F = a.F[i], K = a.K[i], T = a.T[i];
       const int fl = a.flag[i];
-      const double lnbeta = (rg == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, a.P[i], fl) : 0.0;
-      const double s = pivot::solve_region(rg, nd, lnbeta, a.steps);
+      const int rg = bin & 3;
+      const double bb = s_bb[r];
+      const double lnbeta = (rg == pivot::kLower) ? pivot::log_beta(bb, F, K, T, a.P[i], fl) : 0.0;
+      double s = 0.0;
+      if (kMixed && bin < 4) {
+        pivot::Node<float> nf;
+        nf.x = float(s_x[r]);
+        nf.bmax = float(s_bmax[r]);
+        nf.e = float(s_e[r]);
+        nf.bn = float(s_bn[r]);
+        nf.bsn = float(s_bsn[r]);
+        nf.bb = float(bb);
+        s = pivot::solve_region_mixed(rg, nf, s_x[r], bb, lnbeta, a.steps);
+        if (!(s > 0.0 && s < INFINITY)) {
+          // float seed failed: redo the row in double from its inputs
+          const pivot::Quote q = pivot::classify_quote(F, K, T, a.P[i], fl);
+          double x, bmax;
+          pivot::moneyness(F, K, x, bmax);
+          const double rsq = rsqrt(F * K);
+          pivot::Node<double> nd;
+          const int rg2 = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
+          const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, a.P[i], fl) : 0.0;
+          s = pivot::solve_region<double>(rg2, nd, lnb2, a.steps);
+        }
+      } else {
+        pivot::Node<double> nd;
+        nd.x = s_x[r];
+        nd.bmax = s_bmax[r];
+        nd.e = s_e[r];
+        nd.bn = s_bn[r];
+        nd.bsn = s_bsn[r];
+        nd.bb = bb;
+        s = pivot::solve_region<double>(rg, nd, lnbeta, a.steps);
+      }
       const double sig = s / sqrt(T);
       a.sigma[i] = sig;
       if (a.status) a.status[i] = 0;
@@ -260,7 +311,7 @@ int check_opts(const pivot_opts* o, int* steps, int* mode) {
   *steps = kDefaultSteps;
   *mode = PIVOT_MODE_FP64;
   if (o == nullptr) return PIVOT_OK;
-  if (o->mode != PIVOT_MODE_FP64) return PIVOT_E_OPTS;  // other modes: separate entry points
+  if (o->mode != PIVOT_MODE_FP64 && o->mode != PIVOT_MODE_MIXED) return PIVOT_E_OPTS;
   if (o->householder < 0 || o->householder > 4) return PIVOT_E_OPTS;
   if (o->householder > 0) *steps = o->householder;
   *mode = o->mode;
@@ -287,27 +338,32 @@ int select_device(int device) {
 }
 
 // persistent grid for the binned kernels: resident blocks x SMs, capped by the tiles
-template <bool kBackward>
+template <bool kBackward, bool kMixed>
 int launch_binned(const Args& a, void* stream) {
   static thread_local int configured_device = -1;
   static thread_local int blocks_per_sm = 0, num_sms = 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
   if (configured_device != dev) {
-    cudaFuncSetAttribute(k_iv_binned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBinnedSmem));
-    cudaFuncSetAttribute(k_iv_binned<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBinnedSmem));
+    const void* fns[] = {reinterpret_cast<const void*>(k_iv_binned<false, false>),
+                         reinterpret_cast<const void*>(k_iv_binned<true, false>),
+                         reinterpret_cast<const void*>(k_iv_binned<false, true>),
+                         reinterpret_cast<const void*>(k_iv_binned<true, true>)};
+    int bmin = 1 << 30;
+    for (const void* f : fns) {
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBinnedSmem));
+      int b = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, kBinnedSmem);
+      bmin = b < bmin ? b : bmin;
+    }
     cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    int b0 = 0, b1 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_iv_binned<false>, kBlock, kBinnedSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_iv_binned<true>, kBlock, kBinnedSmem);
-    blocks_per_sm = b0 < b1 ? b0 : b1;
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    blocks_per_sm = bmin < 1 ? 1 : bmin;
     configured_device = dev;
   }
   const int64_t tiles = (a.n + kTile - 1) / kTile;
   const int64_t cap = int64_t(blocks_per_sm) * num_sms;
   const unsigned grid = unsigned(tiles < cap ? tiles : cap);
-  k_iv_binned<kBackward><<<grid, kBlock, kBinnedSmem, static_cast<cudaStream_t>(stream)>>>(a);
+  k_iv_binned<kBackward, kMixed><<<grid, kBlock, kBinnedSmem, static_cast<cudaStream_t>(stream)>>>(a);
   return launch_status();
 }
 
@@ -346,7 +402,7 @@ int pivot_iv_forward(int64_t n, const double* F, const double* K, const double* 
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
   Args a{n, F, K, T, P, flag, nullptr, 0.0, 0, steps, sigma_out, status_out, nullptr, nullptr, nullptr, nullptr};
-  return launch_binned<false>(a, stream);
+  return mode == PIVOT_MODE_MIXED ? launch_binned<false, true>(a, stream) : launch_binned<false, false>(a, stream);
 }
 
 int pivot_iv_backward(int64_t n, const double* F, const double* K, const double* T, const int8_t* flag,
@@ -387,7 +443,7 @@ int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
   Args a{n, F, K, T, P, flag, gbar, tau, gate_mode, steps, sigma_out, status_out, dP, dF, dK, dT};
-  return launch_binned<true>(a, stream);
+  return mode == PIVOT_MODE_MIXED ? launch_binned<true, true>(a, stream) : launch_binned<true, false>(a, stream);
 }
 
 const char* pivot_error_string(int code) {

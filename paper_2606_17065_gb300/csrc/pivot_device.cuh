@@ -44,74 +44,122 @@ constexpr double kTaylorX = 0.1;
 
 enum Region : int { kLower = 0, kMidLow = 1, kMidHigh = 2, kUpper = 3 };
 
+// The LBR arithmetic below is written once for both precisions: double for
+// the plain path, float for the guess and first Householder step of the
+// mixed path.  Math<R> maps each function to its CUDA precision variant.
+template <typename R>
+struct Math;
+template <>
+struct Math<double> {
+  static __device__ __forceinline__ double erfcx_(double v) { return ::erfcx(v); }
+  static __device__ __forceinline__ double exp_(double v) { return ::exp(v); }
+  static __device__ __forceinline__ double log_(double v) { return ::log(v); }
+  static __device__ __forceinline__ double sqrt_(double v) { return ::sqrt(v); }
+  static __device__ __forceinline__ double cbrt_(double v) { return ::cbrt(v); }
+  static __device__ __forceinline__ double ncdf_(double v) { return ::normcdf(v); }
+  static __device__ __forceinline__ double ncdfinv_(double v) { return ::normcdfinv(v); }
+  static __device__ __forceinline__ double fma_(double a, double b, double c) { return ::fma(a, b, c); }
+  static __device__ __forceinline__ double fmin_(double a, double b) { return ::fmin(a, b); }
+  static __device__ __forceinline__ double fmax_(double a, double b) { return ::fmax(a, b); }
+  static constexpr double kTiny = 1e-280; // below this beta's cube root is taken through logs
+};
+template <>
+struct Math<float> {
+  static __device__ __forceinline__ float erfcx_(float v) { return ::erfcxf(v); }
+  static __device__ __forceinline__ float exp_(float v) { return ::expf(v); }
+  static __device__ __forceinline__ float log_(float v) { return ::logf(v); }
+  static __device__ __forceinline__ float sqrt_(float v) { return ::sqrtf(v); }
+  static __device__ __forceinline__ float cbrt_(float v) { return ::cbrtf(v); }
+  static __device__ __forceinline__ float ncdf_(float v) { return ::normcdff(v); }
+  static __device__ __forceinline__ float ncdfinv_(float v) { return ::normcdfinvf(v); }
+  static __device__ __forceinline__ float fma_(float a, float b, float c) { return ::fmaf(a, b, c); }
+  static __device__ __forceinline__ float fmin_(float a, float b) { return ::fminf(a, b); }
+  static __device__ __forceinline__ float fmax_(float a, float b) { return ::fmaxf(a, b); }
+  static constexpr float kTiny = 1e-35f;
+};
+
 // Y(z) = Phi(z)/phi(z).  Kept out of line: it is called from many sites and
 // one shared copy keeps the kernels' instruction footprint small.
-__device__ __noinline__ double mills_y(double z) { return kSqrtPiOver2 * erfcx(-z * kInvSqrt2); }
-
-// ln b_s(x, s) = -(h^2 + t^2)/2 - ln sqrt(2 pi)
-__device__ __forceinline__ double log_bs(double h, double t) {
-  return fma(-0.5, fma(h, h, t * t), -kLnSqrt2Pi);
+template <typename R>
+__device__ __noinline__ R mills_y(R z) {
+  return R(kSqrtPiOver2) * Math<R>::erfcx_(-z * R(kInvSqrt2));
 }
 
-__device__ __forceinline__ double rho_taylor(double h, double t) {
-  double c_prev = mills_y(h);           // c_0
-  double c_cur = fma(h, c_prev, 1.0);   // c_1
-  const double t2 = t * t;
-  double acc = c_cur, tp = 1.0;
+// ln b_s(x, s) = -(h^2 + t^2)/2 - ln sqrt(2 pi)
+template <typename R>
+__device__ __forceinline__ R log_bs(R h, R t) {
+  return Math<R>::fma_(R(-0.5), Math<R>::fma_(h, h, t * t), R(-kLnSqrt2Pi));
+}
+
+template <typename R>
+__device__ __forceinline__ R rho_taylor(R h, R t) {
+  R c_prev = mills_y<R>(h);                 // c_0
+  R c_cur = Math<R>::fma_(h, c_prev, R(1)); // c_1
+  const R t2 = t * t;
+  R acc = c_cur, tp = R(1);
   // c_{n+1} = (h c_n + c_{n-1}) / (n + 1), two steps per odd term
 #pragma unroll
   for (int m = 1; m < 9; ++m) {
     const int n = 2 * m - 1;
-    double c_next = fma(h, c_cur, c_prev) * (1.0 / double(n + 1));
+    R c_next = Math<R>::fma_(h, c_cur, c_prev) * R(1.0 / double(n + 1));
     c_prev = c_cur;
     c_cur = c_next;
-    c_next = fma(h, c_cur, c_prev) * (1.0 / double(n + 2));
+    c_next = Math<R>::fma_(h, c_cur, c_prev) * R(1.0 / double(n + 2));
     c_prev = c_cur;
     c_cur = c_next;
     tp *= t2;
-    acc = fma(c_cur, tp, acc);
+    acc = Math<R>::fma_(c_cur, tp, acc);
   }
-  return 2.0 * t * acc;
+  return R(2) * t * acc;
 }
 
 // rho = b / b_s for x <= 0, s > 0
-__device__ __forceinline__ double rho_of(double x, double h, double t) {
-  if (t <= kTaylorT && x >= -kTaylorX) return rho_taylor(h, t);
-  return mills_y(h + t) - mills_y(h - t);
+template <typename R>
+__device__ __forceinline__ R rho_of(R x, R h, R t) {
+  if (t <= R(kTaylorT) && x >= R(-kTaylorX)) return rho_taylor<R>(h, t);
+  return mills_y<R>(h + t) - mills_y<R>(h - t);
 }
 
 // gamma = (b_max - b) / b_s
-__device__ __forceinline__ double gamma_of(double h, double t) { return mills_y(-h - t) + mills_y(h - t); }
+template <typename R>
+__device__ __forceinline__ R gamma_of(R h, R t) {
+  return mills_y<R>(-h - t) + mills_y<R>(h - t);
+}
 
 // Delbourgo-Gregory rational cubic Hermite interpolant on [z0, z1] through
 // (z0, y0), (z1, y1) with end slopes d0, d1 and shape parameter r (r = 3 is
 // the cubic Hermite; larger r pulls towards the chord).
-__device__ __forceinline__ double rational_cubic(double z, double z0, double z1, double y0, double y1,
-                                                 double d0, double d1, double r) {
-  const double D = z1 - z0;
-  const double tau = (z - z0) / D;
-  const double om = 1.0 - tau;
-  const double num = y0 * om * om * om + (r * y0 + D * d0) * tau * om * om + (r * y1 - D * d1) * tau * tau * om +
-                     y1 * tau * tau * tau;
-  const double den = fma((r - 3.0) * tau, om, 1.0);
+template <typename R>
+__device__ __forceinline__ R rational_cubic(R z, R z0, R z1, R y0, R y1, R d0, R d1, R r) {
+  const R D = z1 - z0;
+  const R tau = (z - z0) / D;
+  const R om = R(1) - tau;
+  const R num = y0 * om * om * om + (r * y0 + D * d0) * tau * om * om + (r * y1 - D * d1) * tau * tau * om +
+                y1 * tau * tau * tau;
+  const R den = Math<R>::fma_((r - R(3)) * tau, om, R(1));
   return num / den;
 }
 
 // Shape parameter with zero second derivative at the right end (z1) and at
 // least the monotonicity bound (d0 + d1)/m of the Delbourgo-Gregory form.
-__device__ __forceinline__ double shape_zero_curv_right(double D, double y0, double y1, double d0, double d1) {
-  const double r = D * (d1 - d0) / (D * d1 + y0 - y1);
-  const double rmono = (d0 + d1) * D / (y1 - y0);
-  return fmax(r, rmono);
+// In the interpolant's own parameters S''(1) = 2 (D d0 + (r - 1) D d1 +
+// r (y0 - y1)) / D^2 and S''(0) = -2 ((r - 1) D d0 + D d1 + r (y0 - y1)) / D^2.
+template <typename R>
+__device__ __forceinline__ R shape_zero_curv_right(R D, R y0, R y1, R d0, R d1) {
+  const R r = D * (d1 - d0) / (D * d1 + y0 - y1);
+  const R rmono = (d0 + d1) * D / (y1 - y0);
+  return Math<R>::fmax_(r, rmono);
 }
 // ... zero second derivative at the left end (z0)
-__device__ __forceinline__ double shape_zero_curv_left(double D, double y0, double y1, double d0, double d1) {
-  const double r = D * (d0 - d1) / (D * d0 + y0 - y1);
-  const double rmono = (d0 + d1) * D / (y1 - y0);
-  return fmax(r, rmono);
+template <typename R>
+__device__ __forceinline__ R shape_zero_curv_left(R D, R y0, R y1, R d0, R d1) {
+  const R r = D * (d0 - d1) / (D * d0 + y0 - y1);
+  const R rmono = (d0 + d1) * D / (y1 - y0);
+  return Math<R>::fmax_(r, rmono);
 }
-__device__ __forceinline__ double shape_monotone(double D, double y0, double y1, double d0, double d1) {
-  return fmax(3.0, (d0 + d1) * D / (y1 - y0));
+template <typename R>
+__device__ __forceinline__ R shape_monotone(R D, R y0, R y1, R d0, R d1) {
+  return Math<R>::fmax_(R(3), (d0 + d1) * D / (y1 - y0));
 }
 
 // ---------------------------------------------------------------------------
@@ -206,34 +254,37 @@ __device__ __forceinline__ double log_beta(double beta, double F, double K, doub
 // b_max - b_u = b_s (Y(-h - t) + Y(h - t)).  The node only seeds the guess,
 // so the difference form is accurate enough for it everywhere.
 // ---------------------------------------------------------------------------
+template <typename R>
 struct Node {
-  double x;    // -|ln(F/K)|
-  double bmax; // e^{x/2}
-  double e;    // erfcx(sqrt|x|)
-  double bn;   // b_l (lower side) or b_max - b_u (upper side)
-  double bsn;  // b_s at that node
-  double bb;   // beta, or beta_c = b_max - beta in the upper region
+  R x;    // -|ln(F/K)|
+  R bmax; // e^{x/2}
+  R e;    // erfcx(sqrt|x|)
+  R bn;   // b_l (lower side) or b_max - b_u (upper side)
+  R bsn;  // b_s at that node
+  R bb;   // beta, or beta_c = b_max - beta in the upper region
 };
 
-__device__ __forceinline__ int classify(double x, double bmax, double beta, double betac, Node& nd) {
-  const double ax = -x;
-  const double sc = sqrt(2.0 * ax);
-  const double e = erfcx(sc * kInvSqrt2);
-  const double bc = 0.5 * bmax * (1.0 - e);
+template <typename R>
+__device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& nd) {
+  using M = Math<R>;
+  const R ax = -x;
+  const R sc = M::sqrt_(R(2) * ax);
+  const R e = M::erfcx_(sc * R(kInvSqrt2));
+  const R bc = R(0.5) * bmax * (R(1) - e);
   const bool low = beta <= bc;
-  const double sl = sc - kSqrtPiOver2 * (1.0 - e);
-  const double su = sc + kSqrtPiOver2 * (1.0 + e);
-  const bool has_l = sl > 0.0;
-  const double sn = low ? (has_l ? sl : 1.0) : su;
-  const double h = x / sn, t = 0.5 * sn;
-  const double y1 = mills_y(low ? h + t : -h - t);
-  const double y2 = mills_y(h - t);
-  const double bs = exp(log_bs(h, t));
-  const double val = bs * (low ? y1 - y2 : y1 + y2);
+  const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
+  const R su = sc + R(kSqrtPiOver2) * (R(1) + e);
+  const bool has_l = sl > R(0);
+  const R sn = low ? (has_l ? sl : R(1)) : su;
+  const R h = x / sn, t = R(0.5) * sn;
+  const R y1 = mills_y<R>(low ? h + t : -h - t);
+  const R y2 = mills_y<R>(h - t);
+  const R bs = M::exp_(log_bs<R>(h, t));
+  const R val = bs * (low ? y1 - y2 : y1 + y2);
   nd.x = x;
   nd.bmax = bmax;
   nd.e = e;
-  nd.bn = (low && !has_l) ? 0.0 : val;
+  nd.bn = (low && !has_l) ? R(0) : val;
   nd.bsn = bs;
   int region;
   if (low) region = (beta < nd.bn) ? kLower : kMidLow;
@@ -244,59 +295,61 @@ __device__ __forceinline__ int classify(double x, double bmax, double beta, doub
 
 // Rational initial guess s^(0) of the row's region from its node.
 // lnbeta is ln beta (lower region only).
-__device__ __forceinline__ double region_guess(int region, const Node& nd, double lnbeta) {
-  const double x = nd.x, ax = -x;
-  const double sc = sqrt(2.0 * ax);
-  const double e = nd.e;
-  const double dc = kSqrt2Pi / nd.bmax; // ds/db at s_c
+template <typename R>
+__device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbeta) {
+  using M = Math<R>;
+  const R x = nd.x, ax = -x;
+  const R sc = M::sqrt_(R(2) * ax);
+  const R e = nd.e;
+  const R dc = R(kSqrt2Pi) / nd.bmax; // ds/db at s_c
   switch (region) {
     case kLower: {
       // lower tail: b ~ kappa Phi(-|x|/(sqrt3 s))^3 as s -> 0, kappa = 2 pi |x| / (3 sqrt 3).
       // Interpolate G = Phi(-|x|/(sqrt3 s)) against u = (beta/kappa)^(1/3) on [0, u_l]
       // (G(0) = 0, G'(0) = 1, G(u_l), G'(u_l) exact), then invert G for s.
-      const double sl = sc - kSqrtPiOver2 * (1.0 - e);
-      const double bl = nd.bn, bsl = nd.bsn, beta = nd.bb;
-      const double kap = kTwoPiOver3Sqrt3 * ax;
-      const double u = (beta > 1e-280) ? cbrt(beta / kap) : exp((lnbeta - log(kap)) * (1.0 / 3.0));
-      const double ul = cbrt(bl / kap);
-      const double al = ax * kInvSqrt3 / sl;
-      const double Gl = normcdf(-al);
-      const double dGl = 3.0 * bl * (kInvSqrt2Pi * exp(-0.5 * al * al)) * al / (sl * ul * bsl);
-      const double r = shape_monotone(ul, 0.0, Gl, 1.0, dGl);
-      const double G = fmin(rational_cubic(u, 0.0, ul, 0.0, Gl, 1.0, dGl, r), 0.5);
-      return ax * kInvSqrt3 / (-normcdfinv(G));
+      const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
+      const R bl = nd.bn, bsl = nd.bsn, beta = nd.bb;
+      const R kap = R(kTwoPiOver3Sqrt3) * ax;
+      const R u = (beta > M::kTiny) ? M::cbrt_(beta / kap) : M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
+      const R ul = M::cbrt_(bl / kap);
+      const R al = ax * R(kInvSqrt3) / sl;
+      const R Gl = M::ncdf_(-al);
+      const R dGl = R(3) * bl * (R(kInvSqrt2Pi) * M::exp_(R(-0.5) * al * al)) * al / (sl * ul * bsl);
+      const R r = shape_monotone<R>(ul, R(0), Gl, R(1), dGl);
+      const R G = M::fmin_(rational_cubic<R>(u, R(0), ul, R(0), Gl, R(1), dGl, r), R(0.5));
+      return ax * R(kInvSqrt3) / (-M::ncdfinv_(G));
     }
     case kMidLow: {
       // rational cubic in b on [b_l, b_c], zero curvature of s(b) at the inflection b_c
-      const double sl = sc - kSqrtPiOver2 * (1.0 - e);
-      const double bc = 0.5 * nd.bmax * (1.0 - e);
-      const double bl = nd.bn;
-      const double d0 = (bl > 0.0) ? 1.0 / nd.bsn : dc;
-      const double s0 = (bl > 0.0) ? sl : 0.0;
-      const double D = bc - bl;
-      const double r = shape_zero_curv_right(D, s0, sc, d0, dc);
-      return rational_cubic(nd.bb, bl, bc, s0, sc, d0, dc, r);
+      const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
+      const R bc = R(0.5) * nd.bmax * (R(1) - e);
+      const R bl = nd.bn;
+      const R d0 = (bl > R(0)) ? R(1) / nd.bsn : dc;
+      const R s0 = (bl > R(0)) ? sl : R(0);
+      const R D = bc - bl;
+      const R r = shape_zero_curv_right<R>(D, s0, sc, d0, dc);
+      return rational_cubic<R>(nd.bb, bl, bc, s0, sc, d0, dc, r);
     }
     case kMidHigh: {
       // rational cubic in b on [b_c, b_u], zero curvature of s(b) at b_c
-      const double su = sc + kSqrtPiOver2 * (1.0 + e);
-      const double bc = 0.5 * nd.bmax * (1.0 - e);
-      const double bu = nd.bmax - nd.bn;
-      const double d1 = 1.0 / nd.bsn;
-      const double D = bu - bc;
-      const double r = shape_zero_curv_left(D, sc, su, dc, d1);
-      return rational_cubic(nd.bb, bc, bu, sc, su, dc, d1, r);
+      const R su = sc + R(kSqrtPiOver2) * (R(1) + e);
+      const R bc = R(0.5) * nd.bmax * (R(1) - e);
+      const R bu = nd.bmax - nd.bn;
+      const R d1 = R(1) / nd.bsn;
+      const R D = bu - bc;
+      const R r = shape_zero_curv_left<R>(D, sc, su, dc, d1);
+      return rational_cubic<R>(nd.bb, bc, bu, sc, su, dc, d1, r);
     }
     default: {
       // upper tail: b_max - b ~ 2 Phi(-s/2) as s -> inf.  Interpolate
       // v = Phi(-s/2) against u = (b_max - beta)/2 on [0, u_u], v'(0) = 1.
-      const double su = sc + kSqrtPiOver2 * (1.0 + e);
-      const double uu = 0.5 * nd.bn;
-      const double vu = normcdf(-0.5 * su);
-      const double dvu = (kInvSqrt2Pi * exp(-0.125 * su * su)) / nd.bsn;
-      const double r = shape_monotone(uu, 0.0, vu, 1.0, dvu);
-      const double v = fmin(rational_cubic(0.5 * nd.bb, 0.0, uu, 0.0, vu, 1.0, dvu, r), 0.5);
-      return -2.0 * normcdfinv(v);
+      const R su = sc + R(kSqrtPiOver2) * (R(1) + e);
+      const R uu = R(0.5) * nd.bn;
+      const R vu = M::ncdf_(R(-0.5) * su);
+      const R dvu = (R(kInvSqrt2Pi) * M::exp_(R(-0.125) * su * su)) / nd.bsn;
+      const R r = shape_monotone<R>(uu, R(0), vu, R(1), dvu);
+      const R v = M::fmin_(rational_cubic<R>(R(0.5) * nd.bb, R(0), uu, R(0), vu, R(1), dvu, r), R(0.5));
+      return R(-2) * M::ncdfinv_(v);
     }
   }
 }
@@ -306,53 +359,71 @@ __device__ __forceinline__ double region_guess(int region, const Node& nd, doubl
 //   lower:  f = 1/ln b(s) - 1/ln beta
 //   middle: f = b(s) - beta
 //   upper:  f = ln(b_max - beta) - ln(b_max - b(s))
-// with b''/b' = x^2/s^3 - s/4 and b'''/b' = (b''/b')^2 - 3x^2/s^4 - 1/4:
+// with b2 = b''/b' = x^2/s^3 - s/4 and b3 = b'''/b' = b2^2 - 3x^2/s^4 - 1/4:
 //   s <- s + nu (1 + h2 nu / 2) / (1 + nu (h2 + h3 nu / 6)),
 //   nu = -f/f', h2 = f''/f', h3 = f'''/f'.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double householder_step(double x, double beta, double lnbetac, double inv_lnbeta,
-                                                   int region, double s) {
-  const double inv_s = 1.0 / s;
-  const double h = x * inv_s, t = 0.5 * s;
-  const double hh = h * h;
-  const double b2 = (hh - t * t) * inv_s;                    // b''/b'
-  const double b3 = fma(b2, b2, -3.0 * hh * inv_s * inv_s) - 0.25; // b'''/b'
-  double nu, h2, h3;
+template <typename R>
+__device__ __forceinline__ R householder_step(R x, R beta, R lnbetac, R inv_lnbeta, int region, R s) {
+  using M = Math<R>;
+  const R inv_s = R(1) / s;
+  const R h = x * inv_s, t = R(0.5) * s;
+  const R hh = h * h;
+  const R b2 = (hh - t * t) * inv_s;                                  // b''/b'
+  const R b3 = M::fma_(b2, b2, R(-3) * hh * inv_s * inv_s) - R(0.25); // b'''/b'
+  R nu, h2, h3;
   if (region == kLower) {
-    const double rho = rho_of(x, h, t);
-    const double L = log_bs(h, t) + log(rho); // ln b
-    const double q = 1.0 / rho;               // (ln b)' = b'/b
-    const double iL = 1.0 / L;
+    const R rho = rho_of<R>(x, h, t);
+    const R L = log_bs<R>(h, t) + M::log_(rho); // ln b
+    const R q = R(1) / rho;                     // (ln b)' = b'/b
+    const R iL = R(1) / L;
     // nu = -(1/L - 1/Lb) L^2 / q = rho L (Lb - L) / Lb
-    nu = rho * L * (1.0 - L * inv_lnbeta);
-    h2 = b2 - q * fma(2.0, iL, 1.0);
-    h3 = b3 - 3.0 * b2 * q + 2.0 * q * q - 6.0 * q * (b2 - q) * iL + 6.0 * q * q * iL * iL;
+    nu = rho * L * (R(1) - L * inv_lnbeta);
+    h2 = b2 - q * M::fma_(R(2), iL, R(1));
+    h3 = b3 - R(3) * b2 * q + R(2) * q * q - R(6) * q * (b2 - q) * iL + R(6) * q * q * iL * iL;
   } else if (region == kUpper) {
-    const double gam = gamma_of(h, t);
-    const double pg = 1.0 / gam; // b'/(b_max - b)
-    const double f = lnbetac - log_bs(h, t) - log(gam);
+    const R gam = gamma_of<R>(h, t);
+    const R pg = R(1) / gam; // b'/(b_max - b)
+    const R f = lnbetac - log_bs<R>(h, t) - M::log_(gam);
     nu = -f * gam;
     h2 = b2 + pg;
-    h3 = b3 + 3.0 * pg * b2 + 2.0 * pg * pg;
+    h3 = b3 + R(3) * pg * b2 + R(2) * pg * pg;
   } else {
-    const double rho = rho_of(x, h, t);
-    const double bs = exp(log_bs(h, t));
+    const R rho = rho_of<R>(x, h, t);
+    const R bs = M::exp_(log_bs<R>(h, t));
     nu = beta / bs - rho; // (beta - b)/b'
     h2 = b2;
     h3 = b3;
   }
-  const double num = nu * fma(0.5 * h2, nu, 1.0);
-  const double den = fma(nu, fma(h3 * (1.0 / 6.0), nu, h2), 1.0);
+  const R num = nu * M::fma_(R(0.5) * h2, nu, R(1));
+  const R den = M::fma_(nu, M::fma_(h3 * R(1.0 / 6.0), nu, h2), R(1));
   return s + num / den;
 }
 
 // Guess plus `steps` Householder(3) steps for a classified row; returns s.
-__device__ __forceinline__ double solve_region(int region, const Node& nd, double lnbeta, int steps) {
-  const double lnbetac = (region == kUpper) ? log(nd.bb) : 0.0;
-  const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
-  double s = region_guess(region, nd, lnbeta);
-  for (int i = 0; i < steps; ++i) s = householder_step(nd.x, nd.bb, lnbetac, inv_lnbeta, region, s);
+template <typename R>
+__device__ __forceinline__ R solve_region(int region, const Node<R>& nd, R lnbeta, int steps) {
+  const R lnbetac = (region == kUpper) ? Math<R>::log_(nd.bb) : R(0);
+  const R inv_lnbeta = (region == kLower) ? R(1) / lnbeta : R(0);
+  R s = region_guess<R>(region, nd, lnbeta);
+  for (int i = 0; i < steps; ++i) s = householder_step<R>(nd.x, nd.bb, lnbetac, inv_lnbeta, region, s);
   return s;
+}
+
+// Mixed precision (PIVOT_MODE_MIXED): the float node seeds a float guess and
+// `steps - 1` float Householder steps; the final step runs in double from
+// the double inputs of the row (x, beta or beta_c, ln beta).  Householder(3)
+// converges quartically, so a float iterate within ~1e-4 relative lands at
+// double precision after the one FP64 step.
+__device__ __forceinline__ double solve_region_mixed(int region, const Node<float>& nf, double x, double bb,
+                                                     double lnbeta, int steps) {
+  const float lnbetac_f = (region == kUpper) ? logf(nf.bb) : 0.0f;
+  const float inv_lnbeta_f = (region == kLower) ? 1.0f / float(lnbeta) : 0.0f;
+  float sf = region_guess<float>(region, nf, float(lnbeta));
+  for (int i = 1; i < steps; ++i) sf = householder_step<float>(nf.x, nf.bb, lnbetac_f, inv_lnbeta_f, region, sf);
+  const double lnbetac = (region == kUpper) ? log(bb) : 0.0;
+  const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
+  return householder_step<double>(x, bb, lnbetac, inv_lnbeta, region, double(sf));
 }
 
 // ---------------------------------------------------------------------------
@@ -392,12 +463,12 @@ __device__ __forceinline__ Grad gated_adjoint(double F, double K, double T, int 
   const double s = sigma * sqT;
   const double inv_s = 1.0 / s;
   const double h = xs * inv_s, t = 0.5 * s;
-  const double V = sqrt(F * K) * sqT * exp(log_bs(h, t));
+  const double V = sqrt(F * K) * sqT * exp(log_bs<double>(h, t));
   const double d1 = h + t, d2 = h - t;
   // call: jF = -Y(d1)/(F sqrt T), jK = Y(d2)/(K sqrt T); put: the same of -d1, -d2 with signs flipped
   const double sg = flag > 0 ? 1.0 : -1.0;
-  const double jF = -sg * mills_y(sg * d1) / (F * sqT);
-  const double jK = sg * mills_y(sg * d2) / (K * sqT);
+  const double jF = -sg * mills_y<double>(sg * d1) / (F * sqT);
+  const double jK = sg * mills_y<double>(sg * d2) / (K * sqT);
   const double jT = -sigma / (2.0 * T);
   const bool in_g = fabs(V) > tau;
   if (mode == 0 || (mode <= 2 && in_g)) {
@@ -464,12 +535,12 @@ __device__ __forceinline__ void black_price_row(double F, double K, double T, do
   }
   const double s = sigma * sqT;
   const double h = x / s, t = 0.5 * s;
-  const double bs = exp(log_bs(h, t));
+  const double bs = exp(log_bs<double>(h, t));
   double b;
   if (s > 2.0 && s * s > -2.0 * x) {
-    b = bmax - bs * gamma_of(h, t); // above the inflection and s > 2: b >~ 0.4 b_max
+    b = bmax - bs * gamma_of<double>(h, t); // above the inflection and s > 2: b >~ 0.4 b_max
   } else {
-    b = bs * rho_of(x, h, t);
+    b = bs * rho_of<double>(x, h, t);
   }
   P = intrinsic + rfk * b;
   V = rfk * sqT * bs;

@@ -235,3 +235,58 @@ def test_full_size_stress_sampled():
     ok = st_all == 0
     assert np.all(np.isfinite(sig_all[ok]) & (sig_all[ok] > 0))
     assert np.all(np.isnan(sig_all[np.isin(st_all, [1, 2, 3])]))
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision: float node, guess and first Householder step; FP64 final
+# step, adjoint, and every row outside the float range.  Same bar as FP64.
+# ---------------------------------------------------------------------------
+def test_mixed_forward_parity(body, stress):
+    for name, (b, P, ref, st_ref) in (("body", body), ("stress", stress)):
+        sig, st = gpu_iv(b, P, mode="mixed")
+        assert_sigma_parity(b.F, b.K, b.T, P, b.flag, sig, st, ref, st_ref, where=f"mixed {name}")
+
+
+def test_mixed_fused_parity(body, stress):
+    for name, (b, P, ref, st_ref) in (("body", body), ("stress", stress)):
+        out = pv.iv_forward_backward(to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(P), to_dev(b.flag), tau=1e-6,
+                                     gate="nan", mode="mixed")
+        sig, st, *grads = [to_np(x) for x in out]
+        dom = assert_sigma_parity(b.F, b.K, b.T, P, b.flag, sig, st, ref, st_ref, where=f"mixed fused {name}")
+        want = oracle.iv_grad(b.F, b.K, b.T, b.flag, ref, None, 1e-6, 1, nthreads=0)
+        assert_grad_parity(grads, want, dom, where=f"mixed fused {name}")
+
+
+@pytest.mark.parametrize("steps", [2, 3])
+def test_mixed_edge_cases_and_steps(steps):
+    F, K, T, P, flag = edge_rows()
+    ref, st_ref = oracle.implied_vol(F, K, T, P, flag)
+    sig, st = pv.iv(to_dev(F), to_dev(K), to_dev(T), to_dev(P), to_dev(flag), mode="mixed", householder=steps)
+    assert_sigma_parity(F, K, T, P, flag, to_np(sig), to_np(st), ref, st_ref, where=f"mixed edge steps={steps}")
+
+
+def test_full_size_mixed_sampled():
+    """64M rows of the body distribution (the mixed-precision workload), sampled rows checked one by one."""
+    b = workloads.body_batch(workloads.LARGE_N, seed=3)
+    F, K, T, flag = to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(b.flag)
+    P_dev, _ = pv.black_price(F, K, T, to_dev(b.sigma_star), flag, vega=False)
+    idx = workloads.sample_indices(b.n, 20000, seed=10)
+    sb = b.subset(idx)
+    P_s = oracle_inputs(sb)
+    tidx = torch.from_numpy(idx).to(DEV)
+    P_dev[tidx] = torch.from_numpy(P_s).to(DEV)
+    sig, st, dP, dF, dK, dT = pv.iv_forward_backward(F, K, T, P_dev, flag, tau=1e-6, gate="nan", mode="mixed")
+    torch.cuda.synchronize()
+    ref, st_ref = oracle.implied_vol(sb.F, sb.K, sb.T, P_s, sb.flag, nthreads=0)
+    dom = assert_sigma_parity(sb.F, sb.K, sb.T, P_s, sb.flag, to_np(sig[tidx]), to_np(st[tidx]), ref, st_ref,
+                              where="64M mixed sample")
+    want = oracle.iv_grad(sb.F, sb.K, sb.T, sb.flag, ref, None, 1e-6, 1, nthreads=0)
+    assert_grad_parity([to_np(g[tidx]) for g in (dP, dF, dK, dT)], want, dom, where="64M mixed sample")
+    # every row: the mixed result equals the plain FP64 result to the same bar
+    sig64, st64 = pv.iv(F, K, T, P_dev, flag, mode="fp64")
+    assert torch.equal(st, st64)
+    ok = st64 == 0
+    rel = ((sig[ok] - sig64[ok]).abs() / sig64[ok]).max().item()
+    assert rel <= 2e-13, rel
+    del F, K, T, flag, P_dev, sig, st, dP, dF, dK, dT, sig64, st64
+    torch.cuda.empty_cache()
