@@ -215,6 +215,65 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def time_variant(fn, n, stream, reps):
+    """Mean ms per call of fn (after 2 untimed calls) on `stream`, and its rate."""
+    import torch
+    for _ in range(2):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms}
+
+
+def body_variants(dev, stream, steps):
+    """The 64M-option body batch (ln K/F ~ U[-1,1], sigma* ~ U[0.05,1]): plain FP64 against
+    the mixed form, fwd+bwd, same launch configuration."""
+    import ctypes
+
+    import torch
+
+    import paper_2606_17065_gb300 as pv
+    from paper_2606_17065_gb300 import _native
+    b = workloads.body_batch(workloads.LARGE_N, seed=3)
+    n = b.n
+    F, K, T = (torch.from_numpy(a).to(dev) for a in (b.F, b.K, b.T))
+    flag = torch.from_numpy(b.flag).to(dev)
+    P, _ = pv.black_price(F, K, T, torch.from_numpy(b.sigma_star).to(dev), flag, vega=False)
+    sig = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+    g = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
+    lib = _native.lib()
+    p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    opts = _native.PivotOpts()
+
+    def run(mode):
+        opts.mode, opts.householder = mode, 0
+        rc = lib.pivot_iv_forward_backward(n, p(F), p(K), p(T), p(P), p(flag), None, TAU, pv.GATES[GATE], p(sig),
+                                           p(st), *[p(x) for x in g], ctypes.byref(opts),
+                                           ctypes.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise RuntimeError(_native.error_string(rc))
+
+    plain = time_variant(lambda: run(0), n, stream, steps)
+    mixed = time_variant(lambda: run(1), n, stream, steps)
+    run(0)
+    s64 = sig.clone()
+    run(1)
+    ok = st == 0
+    _, V = pv.black_price(F, K, T, torch.where(ok, s64, torch.ones_like(s64)), flag)
+    dom = ok & (P <= 100 * s64 * V)
+    mixed["max_rel_sigma_vs_fp64_on_parity_domain"] = float(((sig[dom] - s64[dom]).abs() / s64[dom]).max())
+    del F, K, T, flag, P, sig, st, g, s64, V, dom
+    torch.cuda.empty_cache()
+    return {"workload": "body-64M: F=100, ln(K/F)~U[-1,1], T~U[1/365,3], sigma*~U[0.05,1], fwd+bwd",
+            "rows": n, "plain_fp64": plain, "mixed": mixed,
+            "mixed_speedup": plain["ms_per_step"] / mixed["ms_per_step"]}
 def run_ours(args, rank, world):
     import torch
 
@@ -248,7 +307,8 @@ def run_ours(args, rank, world):
     opts = _native.PivotOpts()
     opts.mode, opts.householder = 0, 0
 
-    def step():
+    def step(mode=0):
+        opts.mode = mode
         rc = lib.pivot_iv_forward_backward(n, p(F), p(K), p(T), p(P), p(flag), None, TAU, pv.GATES[GATE],
                                            p(outs["sigma"]), p(outs["status"]), *[p(g) for g in outs["grads"]],
                                            ctypes.byref(opts), sptr)
@@ -256,6 +316,7 @@ def run_ours(args, rank, world):
             raise RuntimeError(f"pivot_iv_forward_backward failed: {_native.error_string(rc)}")
 
     def step_fwd():
+        opts.mode = 0
         rc = lib.pivot_iv_forward(n, p(F), p(K), p(T), p(P), p(flag), p(outs["sigma"]), p(outs["status"]),
                                   ctypes.byref(opts), sptr)
         if rc != 0:
@@ -282,6 +343,9 @@ def run_ours(args, rank, world):
     ms_per_step = total_ms / args.steps
     value = n * world / (ms_per_step * 1e-3)
     clk = clocks.summary()
+
+    # ---- the mixed-precision form on the same batch (float seed, FP64 final step)
+    mixed = time_variant(lambda: step(mode=1), n, stream, max(args.steps // 2, 2))
 
     # ---- forward-only throughput (same inputs), for context
     for _ in range(2):
@@ -329,6 +393,8 @@ def run_ours(args, rank, world):
     roof["hbm"] = {"achieved": BYTES_PER_ROW * n / (mean_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                    "frac": BYTES_PER_ROW * n / (mean_ms * 1e-3) / 1e9 / hbm_peak}
 
+    body = body_variants(dev, stream, max(args.steps // 4, 2)) if args.rows == workloads.STRESS_N else None
+
     cpu = None
     if rank == 0 and world == 1:
         r, threads, m, dt = oracle_rate(args.cpu_seconds)
@@ -347,6 +413,9 @@ def run_ours(args, rank, world):
                 "gpu_launches": args.steps,
                 "roofline": roof,
                 "forward_only": {"value": n * world / (fwd_ms * 1e-3), "unit": UNIT, "ms_per_step": fwd_ms},
+                "variants": {"mixed_same_workload": mixed,
+                             "mixed_speedup_same_workload": ms_per_step / mixed["ms_per_step"],
+                             "body_64M": body},
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
 
