@@ -111,7 +111,7 @@ __device__ __forceinline__ int warp_append(bool take, int* counter, int lane) {
 }
 
 template <bool kBackward, bool kMixed>
-__global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
+__global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
   extern __shared__ double smem[];
   double* s_x = smem;
   double* s_bmax = s_x + kTile;
@@ -259,10 +259,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_iv_binned(Args a) {
         nd.bb = bb;
         s = pivot::solve_region<double>(rg, nd, lnbeta, a.steps);
       }
-      const double sig = s / sqrt(T);
+      const double inv_sqT = rsqrt(T);
+      const double sig = s * inv_sqT;
       a.sigma[i] = sig;
       if (a.status) a.status[i] = 0;
-      if (kBackward) write_grad(a, i, F, K, T, fl, sig);
+      if (kBackward) {
+        // the adjoint at the solved s, reusing x and 1/sqrt(T) of this row
+        const double g = a.gbar ? a.gbar[i] : 1.0;
+        const double xs = (F >= K) ? -s_x[r] : s_x[r];
+        const pivot::Grad d = isnan(g) ? pivot::degenerate_grad(true, g, a.mode)
+                                       : pivot::adjoint_core(F, K, fl, sig, s, xs, inv_sqT, rsqrt(F * K), g,
+                                                             a.tau, a.mode);
+        if (a.dP) a.dP[i] = d.dP;
+        if (a.dF) a.dF[i] = d.dF;
+        if (a.dK) a.dK[i] = d.dK;
+        if (a.dT) a.dT[i] = d.dT;
+      }
     }
     __syncthreads();
   }

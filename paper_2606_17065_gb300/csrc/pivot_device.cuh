@@ -442,34 +442,38 @@ __device__ __forceinline__ double signed_log_moneyness(double F, double K) {
   return F >= K ? -l : l;
 }
 
-__device__ __forceinline__ Grad gated_adjoint(double F, double K, double T, int flag, double sigma, double g,
-                                              double tau, int mode) {
+// Gradient of a row whose sigma is not finite and positive: invalid rows
+// (NaN sigma, bad inputs) are NaN in every mode; rows on a bound of the price
+// interval (sigma = 0 or +inf) have V = 0 and sit outside every G_tau.
+__device__ __forceinline__ Grad degenerate_grad(bool invalid, double g, int mode) {
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-  Grad out;
-  if (bad_inputs(F, K, T, flag) || !(sigma >= 0.0) || isnan(g)) {
-    out.dP = out.dF = out.dK = out.dT = qnan;
-    return out;
-  }
-  if (sigma == 0.0 || sigma == INFINITY) {
-    // on a bound of the price interval: V = 0, outside every G_tau
-    double v = qnan;
+  double v = qnan;
+  if (!invalid) {
     if (mode == 1) v = (g == 0.0) ? 0.0 : qnan;
     if (mode >= 2) v = 0.0;
-    out.dP = out.dF = out.dK = out.dT = v;
-    return out;
   }
-  const double xs = signed_log_moneyness(F, K);
-  const double sqT = sqrt(T);
-  const double s = sigma * sqT;
-  const double inv_s = 1.0 / s;
-  const double h = xs * inv_s, t = 0.5 * s;
-  const double V = sqrt(F * K) * sqT * exp(log_bs<double>(h, t));
+  Grad out;
+  out.dP = out.dF = out.dK = out.dT = v;
+  return out;
+}
+
+// The gated adjoint of a row with finite sigma > 0, from quantities the
+// caller may already hold: s = sigma sqrt(T), xs = ln(F/K) (signed),
+// inv_sqT = 1/sqrt(T), rsq = 1/sqrt(F K).  1/F = K rsq^2, 1/K = F rsq^2 and
+// V = sqrt(FK) sqrt(T) b_s keep it to one division and one exp besides Y.
+__device__ __forceinline__ Grad adjoint_core(double F, double K, int flag, double sigma, double s, double xs,
+                                             double inv_sqT, double rsq, double g, double tau, int mode) {
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  Grad out;
+  const double h = xs / s, t = 0.5 * s;
+  const double rsq2 = rsq * rsq;
+  const double V = exp(log_bs<double>(h, t)) * (F * K * rsq) / inv_sqT;
   const double d1 = h + t, d2 = h - t;
   // call: jF = -Y(d1)/(F sqrt T), jK = Y(d2)/(K sqrt T); put: the same of -d1, -d2 with signs flipped
   const double sg = flag > 0 ? 1.0 : -1.0;
-  const double jF = -sg * mills_y<double>(sg * d1) / (F * sqT);
-  const double jK = sg * mills_y<double>(sg * d2) / (K * sqT);
-  const double jT = -sigma / (2.0 * T);
+  const double jF = -sg * mills_y<double>(sg * d1) * (K * rsq2) * inv_sqT;
+  const double jK = sg * mills_y<double>(sg * d2) * (F * rsq2) * inv_sqT;
+  const double jT = -0.5 * sigma * inv_sqT * inv_sqT;
   const bool in_g = fabs(V) > tau;
   if (mode == 0 || (mode <= 2 && in_g)) {
     out.dP = g / V;
@@ -490,20 +494,32 @@ __device__ __forceinline__ Grad gated_adjoint(double F, double K, double T, int 
   // smooth gate w = V^2/(V^2 + tau^2) on every row; w/V = V/(V^2 + tau^2)
   double w, wP;
   if (V > tau) {
-    const double r = tau / V;
+    const double inv_V = 1.0 / V;
+    const double r = tau * inv_V;
     w = 1.0 / fma(r, r, 1.0);
-    wP = w / V;
+    wP = w * inv_V;
   } else {
-    const double r = V / tau;
+    const double inv_tau = 1.0 / tau;
+    const double r = V * inv_tau;
     const double den = 1.0 / fma(r, r, 1.0);
     w = r * r * den;
-    wP = (r / tau) * den;
+    wP = r * inv_tau * den;
   }
   out.dP = g * wP;
   out.dF = g * jF * w;
   out.dK = g * jK * w;
   out.dT = g * jT * w;
   return out;
+}
+
+__device__ __forceinline__ Grad gated_adjoint(double F, double K, double T, int flag, double sigma, double g,
+                                              double tau, int mode) {
+  if (bad_inputs(F, K, T, flag) || !(sigma >= 0.0) || isnan(g)) return degenerate_grad(true, g, mode);
+  if (sigma == 0.0 || sigma == INFINITY) return degenerate_grad(false, g, mode);
+  const double xs = signed_log_moneyness(F, K);
+  const double inv_sqT = rsqrt(T);
+  const double s = sigma / inv_sqT;
+  return adjoint_core(F, K, flag, sigma, s, xs, inv_sqT, rsqrt(F * K), g, tau, mode);
 }
 
 // ---------------------------------------------------------------------------
