@@ -82,6 +82,22 @@ int pivot_black_price(int64_t n, const double* F, const double* K, const double*
                       double* vega_out, void* stream);
 
 /*
+ * pivot_black_price_backward -- vector-Jacobian product of the Black-76 price
+ * (r = 0) in (sigma, F, K, T) (Eq. app_black76; vega Eq. app_vega_closed_form):
+ *   dsigma = gbar V,  dF = gbar dP/dF,  dK = gbar dP/dK,  dT = gbar V sigma / (2T),
+ * with dP/dF = Phi(d1) (call) or -Phi(-d1) (put), dP/dK = -Phi(d2) (call) or
+ * Phi(-d2) (put).  This is the smooth price node through which an IV-space
+ * loss reaches a pricer (Section 3.2, "Differentiable IV inside the loss").
+ *   in : F, K, T, sigma (n float64), flag (n int8), gbar (n float64; NULL = 1)
+ *   out: dsigma, dF, dK, dT (n float64 each, any may be NULL)
+ * sigma = 0 gives the one-sided limits (delta of the intrinsic value, V = 0
+ * except at the money); invalid rows give NaN.
+ */
+int pivot_black_price_backward(int64_t n, const double* F, const double* K, const double* T,
+                               const double* sigma, const int8_t* flag, const double* gbar,
+                               double* dsigma, double* dF, double* dK, double* dT, void* stream);
+
+/*
  * pivot_iv_forward -- implied volatility, Algorithm 1 (forward): normalise to
  * (x, beta) with beta = (P - intrinsic)/sqrt(F K), solve b(x, s) = beta in LBR
  * form (appendix stages 1-5), return sigma = s / sqrt(T).

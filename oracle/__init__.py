@@ -47,7 +47,9 @@ def _bind(lib):
     lib.oracle_black_price.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.oracle_iv.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.oracle_iv_grad.argtypes = [i64, vp, vp, vp, vp, vp, vp, d, i32, vp, vp, vp, vp, i32]
-    for name in ("oracle_black_price", "oracle_iv", "oracle_iv_grad", "oracle_max_threads"):
+    lib.oracle_black_price_grad.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    for name in ("oracle_black_price", "oracle_iv", "oracle_iv_grad", "oracle_black_price_grad",
+                 "oracle_max_threads"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -134,6 +136,19 @@ class Oracle:
             raise ValueError(f"oracle_iv returned {rc}")
         return sig, st
 
+    def black_price_grad(self, F, K, T, sigma, flag, gbar=None, nthreads: int = 1):
+        """(dsigma, dF, dK, dT): VJP of the Black-76 price, Eq. app_black76 differentiated."""
+        F, K, T, sigma = map(_f64, (F, K, T, sigma))
+        flag = np.ascontiguousarray(flag, dtype=np.int8)
+        g = None if gbar is None else _f64(gbar)
+        n = F.shape[0]
+        out = [np.empty(n) for _ in range(4)]
+        rc = self.lib.oracle_black_price_grad(n, _ptr(F), _ptr(K), _ptr(T), _ptr(sigma), _ptr(flag), _ptr(g),
+                                              *[_ptr(o) for o in out], nthreads)
+        if rc:
+            raise ValueError(f"oracle_black_price_grad returned {rc}")
+        return tuple(out)
+
     def iv_grad(self, F, K, T, flag, sigma, gbar=None, tau: float = 0.0, gate_mode: int = 0, nthreads: int = 1):
         """(dP, dF, dK, dT): gated IFT vector-Jacobian product, Eq. method_vjp and Section 3.3."""
         F, K, T, sigma = map(_f64, (F, K, T, sigma))
@@ -146,6 +161,10 @@ class Oracle:
         if rc:
             raise ValueError(f"oracle_iv_grad returned {rc}")
         return tuple(out)
+
+
+def black_price_grad(*a, **k):
+    return default().black_price_grad(*a, **k)
 
 
 def default() -> Oracle:

@@ -550,3 +550,63 @@ int oracle_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------------------
+ * Vector-Jacobian product of the Black-76 price (r = 0) in (sigma, F, K, T),
+ * straight from differentiating Eq. app_black76:
+ *   dP/dsigma = V = F phi(d1) sqrt(T),       dP/dT = V sigma / (2T),
+ *   dP/dF = Phi(d1) (call), Phi(d1) - 1 (put),
+ *   dP/dK = -Phi(d2) (call), 1 - Phi(d2) (put),
+ * Phi(z) = erfc(-z/sqrt 2)/2.  sigma = 0: one-sided limits of the intrinsic
+ * value (1/2 at the money); sigma = +inf: the upper bound F (call) or K (put).
+ * ------------------------------------------------------------------------- */
+static double Phi(double z) { return 0.5 * erfc(-z / sqrt(2.0)); }
+
+static void price_grad_row(double F, double K, double T, double sig, int8_t flag, double g, double out[4]) {
+  if (bad_inputs(F, K, T, flag) || !(sig >= 0.0) || isnan(g)) {
+    out[0] = out[1] = out[2] = out[3] = NAN;
+    return;
+  }
+  int theta = flag;
+  double x = log_moneyness(F, K);
+  if (sig == 0.0 || isinf(sig)) {
+    double dF, dK, V = 0.0;
+    if (sig == 0.0) {
+      double itm = theta * x > 0.0 ? 1.0 : (x == 0.0 ? 0.5 : 0.0);
+      dF = theta * itm;
+      dK = -theta * itm;
+      if (x == 0.0) V = sqrt_FK(F, K) * sqrt(T) / sqrt(2.0 * PI);
+    } else {
+      dF = theta > 0 ? 1.0 : 0.0;
+      dK = theta > 0 ? 0.0 : 1.0;
+    }
+    out[0] = g * V; out[1] = g * dF; out[2] = g * dK; out[3] = 0.0;
+    return;
+  }
+  double sqT = sqrt(T), s = sig * sqT;
+  double d1 = x / s + 0.5 * s, d2 = d1 - s;
+  double V = F * exp(-0.5 * d1 * d1) / sqrt(2.0 * PI) * sqT;
+  double dF = theta > 0 ? Phi(d1) : -Phi(-d1);
+  double dK = theta > 0 ? -Phi(d2) : Phi(-d2);
+  out[0] = g * V; out[1] = g * dF; out[2] = g * dK; out[3] = g * V * sig / (2.0 * T);
+}
+
+int oracle_black_price_grad(int64_t n, const double* F, const double* K, const double* T, const double* sigma,
+                            const int8_t* flag, const double* gbar, double* dsigma, double* dF, double* dK,
+                            double* dT, int nthreads) {
+  if (n < 0) return 1;
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(static) num_threads(nt)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    double o[4];
+    price_grad_row(F[i], K[i], T[i], sigma[i], flag[i], gbar ? gbar[i] : 1.0, o);
+    if (dsigma) dsigma[i] = o[0];
+    if (dF) dF[i] = o[1];
+    if (dK) dK[i] = o[2];
+    if (dT) dT[i] = o[3];
+  }
+  (void)nthreads;
+  return 0;
+}

@@ -44,6 +44,10 @@ int oracle_iv_grad(int64_t n, const double* F, const double* K, const double* T,
                    const int8_t* flag, const double* sigma, const double* gbar,
                    double tau, int gate_mode, double* dP, double* dF, double* dK,
                    double* dT, int nthreads);
+/* VJP of the Black-76 price in (sigma, F, K, T); gbar may be NULL (= 1) */
+int oracle_black_price_grad(int64_t n, const double* F, const double* K, const double* T,
+                            const double* sigma, const int8_t* flag, const double* gbar,
+                            double* dsigma, double* dF, double* dK, double* dT, int nthreads);
 /* number of threads OpenMP would use for nthreads <= 0 */
 int oracle_max_threads(void);
 

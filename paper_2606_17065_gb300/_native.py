@@ -24,6 +24,7 @@ class PivotOpts(ctypes.Structure):
 
 _SIGNATURES = {
     "pivot_black_price": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
+    "pivot_black_price_backward": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
     "pivot_iv_forward": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
     "pivot_iv_backward": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp],
     "pivot_iv_forward_backward": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_vp, c_vp,

@@ -92,6 +92,20 @@ def black_price(F, K, T, sigma, flag, *, vega: bool = True):
     return tuple(_host_result((F, K, T, sigma, flag), [P, V]))
 
 
+def black_price_backward(F, K, T, sigma, flag, gbar=None):
+    """VJP of the Black-76 price (r = 0) in (sigma, F, K, T); returns (dsigma, dF, dK, dT)."""
+    dev = _device_of(F, K, T, sigma, flag, gbar)
+    f, k, t, s = (_on(a, dev, torch.float64) for a in (F, K, T, sigma))
+    fl = _on(flag, dev, torch.int8)
+    g = _on(gbar, dev, torch.float64)
+    n = f.numel()
+    _check_lengths(n, k, t, s, fl, g)
+    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
+    _native.call("pivot_black_price_backward", n, _p(f), _p(k), _p(t), _p(s), _p(fl), _p(g),
+                 *[_p(o) for o in outs], _stream(dev))
+    return tuple(_host_result((F, K, T, sigma, flag, gbar), outs))
+
+
 def _opts(mode, householder):
     o = _native.PivotOpts()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -172,3 +186,31 @@ class ImpliedVol(torch.autograd.Function):
 def implied_volatility_autograd(P, F, K, T, flag, tau: float = 1e-6, gate="nan"):
     """Differentiable implied volatility (the paper's operator), see ``ImpliedVol``."""
     return ImpliedVol.apply(P, F, K, T, flag, tau, gate)
+
+
+class BlackPrice(torch.autograd.Function):
+    """P = Black-76 price (r = 0) of (sigma; F, K, T, flag) as an autograd node.
+
+    The smooth price node of Section 3.2: its backward inserts the vega that
+    cancels the 1/vega of ``ImpliedVol`` in a composed loss (the two-vega
+    identity of the SPX appendix).
+    """
+
+    @staticmethod
+    def forward(ctx, sigma, F, K, T, flag):
+        P, _ = black_price(F.detach(), K.detach(), T.detach(), sigma.detach(), flag, vega=False)
+        ctx.save_for_backward(F.detach(), K.detach(), T.detach(), sigma.detach(), flag)
+        return P
+
+    @staticmethod
+    def backward(ctx, gP):
+        F, K, T, sigma, flag = ctx.saved_tensors
+        ds, dF, dK, dT = black_price_backward(F, K, T, sigma, flag, gP.contiguous())
+        need = ctx.needs_input_grad
+        return (ds if need[0] else None, dF if need[1] else None, dK if need[2] else None,
+                dT if need[3] else None, None)
+
+
+def black_price_autograd(sigma, F, K, T, flag):
+    """Differentiable Black-76 price, see ``BlackPrice``."""
+    return BlackPrice.apply(sigma, F, K, T, flag)

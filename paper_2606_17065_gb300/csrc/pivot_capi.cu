@@ -31,6 +31,21 @@ __global__ void __launch_bounds__(kBlock) k_black_price(int64_t n, const double*
   }
 }
 
+__global__ void __launch_bounds__(kBlock) k_black_price_backward(
+    int64_t n, const double* __restrict__ F, const double* __restrict__ K, const double* __restrict__ T,
+    const double* __restrict__ sigma, const int8_t* __restrict__ flag, const double* __restrict__ gbar,
+    double* __restrict__ dsigma, double* __restrict__ dF, double* __restrict__ dK, double* __restrict__ dT) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double g = gbar ? gbar[i] : 1.0;
+    const pivot::PriceGrad d = pivot::black_price_vjp_row(F[i], K[i], T[i], sigma[i], flag[i], g);
+    if (dsigma) dsigma[i] = d.dsigma;
+    if (dF) dF[i] = d.dF;
+    if (dK) dK[i] = d.dK;
+    if (dT) dT[i] = d.dT;
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_iv_backward(int64_t n, const double* __restrict__ F,
                                                         const double* __restrict__ K, const double* __restrict__ T,
                                                         const int8_t* __restrict__ flag,
@@ -395,6 +410,23 @@ int pivot_black_price(int64_t n, const double* F, const double* K, const double*
   if (rc != PIVOT_OK) return rc;
   k_black_price<<<grid_for(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(n, F, K, T, sigma, flag, P_out,
                                                                                   vega_out);
+  return launch_status();
+}
+
+int pivot_black_price_backward(int64_t n, const double* F, const double* K, const double* T,
+                               const double* sigma, const int8_t* flag, const double* gbar, double* dsigma,
+                               double* dF, double* dK, double* dT, void* stream) {
+  if (n < 0) return PIVOT_E_SIZE;
+  if (n == 0) return PIVOT_OK;
+  int dev = -1;
+  const Ptr ps[] = {{F, true, true},        {K, true, true},      {T, true, true},  {sigma, true, true},
+                    {flag, true, false},    {gbar, false, true},  {dsigma, false, true}, {dF, false, true},
+                    {dK, false, true},      {dT, false, true}};
+  int rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  k_black_price_backward<<<grid_for(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(n, F, K, T, sigma, flag,
+                                                                                           gbar, dsigma, dF, dK, dT);
   return launch_status();
 }
 

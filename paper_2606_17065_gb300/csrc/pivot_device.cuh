@@ -562,4 +562,56 @@ __device__ __forceinline__ void black_price_row(double F, double K, double T, do
   V = rfk * sqT * bs;
 }
 
+// ---------------------------------------------------------------------------
+// VJP of the Black-76 price (r = 0) in (sigma, F, K, T).
+// Phi(z) = erfc(-z/sqrt 2)/2 has no cancellation on either tail.
+// ---------------------------------------------------------------------------
+struct PriceGrad {
+  double dsigma, dF, dK, dT;
+};
+
+__device__ __forceinline__ PriceGrad black_price_vjp_row(double F, double K, double T, double sigma, int flag,
+                                                         double g) {
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  PriceGrad o;
+  if (bad_inputs(F, K, T, flag) || !(sigma >= 0.0) || isnan(g)) {
+    o.dsigma = o.dF = o.dK = o.dT = qnan;
+    return o;
+  }
+  const double sg = flag > 0 ? 1.0 : -1.0;
+  const double xs = signed_log_moneyness(F, K);
+  if (sigma == 0.0 || sigma == INFINITY) {
+    // one-sided limits: the price is the intrinsic value (sigma = 0) or the upper bound
+    const bool itm = sg * xs > 0.0;
+    const double half = (xs == 0.0) ? 0.5 : 0.0;
+    double dPdF, dPdK;
+    if (sigma == 0.0) {
+      dPdF = sg * (itm ? 1.0 : half);
+      dPdK = -sg * (itm ? 1.0 : half);
+    } else {
+      dPdF = flag > 0 ? 1.0 : 0.0;
+      dPdK = flag > 0 ? 0.0 : 1.0;
+    }
+    const double V0 = (sigma == 0.0 && xs == 0.0) ? sqrt(F * K) * sqrt(T) * kInvSqrt2Pi : 0.0;
+    o.dsigma = g * V0;
+    o.dF = g * dPdF;
+    o.dK = g * dPdK;
+    o.dT = 0.0;
+    return o;
+  }
+  const double sqT = sqrt(T);
+  const double s = sigma * sqT;
+  const double h = xs / s, t = 0.5 * s;
+  const double V = sqrt(F * K) * sqT * exp(log_bs<double>(h, t));
+  const double d1 = h + t, d2 = h - t;
+  // call: dP/dF = Phi(d1), dP/dK = -Phi(d2); put: dP/dF = -Phi(-d1), dP/dK = Phi(-d2)
+  const double dPdF = sg * 0.5 * erfc(-sg * d1 * kInvSqrt2);
+  const double dPdK = -sg * 0.5 * erfc(-sg * d2 * kInvSqrt2);
+  o.dsigma = g * V;
+  o.dF = g * dPdF;
+  o.dK = g * dPdK;
+  o.dT = g * V * sigma / (2.0 * T);
+  return o;
+}
+
 }  // namespace pivot

@@ -116,3 +116,62 @@ def sample_indices(n: int, m: int, seed: int = 12345) -> np.ndarray:
     rng = np.random.default_rng(seed)
     m = min(m, n)
     return np.sort(rng.choice(n, size=m, replace=False))
+
+
+@dataclass
+class SVIBatch:
+    """Ragged quotes on synthetic SVI surfaces (flat arrays, one entry per quote)."""
+    surface: np.ndarray  # int32 surface index of each quote
+    slot: np.ndarray     # int32 position of the quote within its surface
+    k: np.ndarray        # ln(K/F)
+    F: np.ndarray
+    K: np.ndarray
+    T: np.ndarray
+    flag: np.ndarray
+    sigma_star: np.ndarray
+    n_surfaces: int
+    max_quotes: int
+
+    @property
+    def n(self) -> int:
+        return int(self.F.shape[0])
+
+
+SVI_MATURITIES = (1 / 12, 1 / 6, 1 / 4, 1 / 2, 3 / 4, 1.0, 1.5, 2.0)
+
+
+def svi_batch(n_surfaces: int = 1024, seed: int = 5, min_quotes: int = 50, max_quotes: int = 400) -> SVIBatch:
+    """Synthetic raw-SVI surfaces (the parameterisation the paper cites in its appendix on IV as the
+    working coordinate): a ~ U[.01,.05], b ~ U[.05,.3], rho ~ U[-.8,.2], m ~ U[-.1,.1],
+    s ~ U[.05,.3]; 50-400 quotes per surface over 8 maturities, k = ln(K/F) ~ U[-0.3, 0.3], F = 100.
+    w(k) = a + b (rho (k - m) + sqrt((k - m)^2 + s^2)) is read as annualised variance, sigma = sqrt(w).
+    """
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.01, 0.05, n_surfaces)
+    b = rng.uniform(0.05, 0.3, n_surfaces)
+    rho = rng.uniform(-0.8, 0.2, n_surfaces)
+    m = rng.uniform(-0.1, 0.1, n_surfaces)
+    s = rng.uniform(0.05, 0.3, n_surfaces)
+    nq = rng.integers(min_quotes, max_quotes + 1, n_surfaces)
+    surface = np.repeat(np.arange(n_surfaces, dtype=np.int32), nq)
+    slot = np.concatenate([np.arange(q, dtype=np.int32) for q in nq])
+    n = surface.shape[0]
+    k = rng.uniform(-0.3, 0.3, n)
+    T = np.asarray(SVI_MATURITIES)[rng.integers(0, len(SVI_MATURITIES), n)]
+    km = k - m[surface]
+    w = a[surface] + b[surface] * (rho[surface] * km + np.sqrt(km * km + s[surface] ** 2))
+    F = np.full(n, 100.0)
+    return SVIBatch(surface, slot, k, F, F * np.exp(k), T, _flags(rng, n), np.sqrt(w), n_surfaces, int(nq.max()))
+
+
+def low_vega_chain(n: int = 65536, seed: int = 31) -> Batch:
+    """The paper's low-vega stress chain (appendix, NaN-poisoning diagnostic): deep wings,
+    T log-uniform on [1e-8, 10^-0.5] years, |ln(K/F)| <= 2.5, out-of-the-money quotes, F = 100,
+    sigma* ~ U[0.05, 1] (the paper does not give its sigma range)."""
+    rng = np.random.default_rng(seed)
+    F = np.full(n, 100.0)
+    k = rng.uniform(-2.5, 2.5, n)
+    T = np.exp(rng.uniform(np.log(1e-8), np.log(10 ** -0.5), n))
+    sig = rng.uniform(0.05, 1.0, n)
+    flag = np.where(k > 0, 1, -1).astype(np.int8)
+    return Batch(F, F * np.exp(k), T, sig, flag)

@@ -310,3 +310,22 @@ def test_planted_mistakes_are_caught(tmp_path, name, old, new):
     hom = np.abs(b.F * g_bad[1] + b.K * g_bad[2] + P * g_bad[0])
     caught.append(bool(np.any(hom > 1e-10 * (np.abs(b.F * g_ok[1]) + np.abs(P * g_ok[0])))))
     assert any(caught), name
+
+
+def test_black_price_gradient_against_finite_differences():
+    """dP/d(sigma, F, K, T) of Eq. app_black76 against 50-digit central differences."""
+    b = workloads.body_batch(24, seed=91)
+    got = oracle.black_price_grad(b.F, b.K, b.T, b.sigma_star, b.flag)
+    for i in range(b.n):
+        args = [b.F[i], b.K[i], b.T[i], b.sigma_star[i]]
+        with mp.workdps(50):
+            base = [mp.mpf(a) for a in args]
+            ref = []
+            for j in (3, 0, 1, 2):  # sigma, F, K, T
+                h = base[j] * mp.mpf("1e-18")
+                up, dn = list(base), list(base)
+                up[j] += h
+                dn[j] -= h
+                ref.append((R.price(*up, int(b.flag[i])) - R.price(*dn, int(b.flag[i]))) / (2 * h))
+        for g, r in zip((got[0][i], got[1][i], got[2][i], got[3][i]), ref):
+            assert abs(g - float(r)) <= 1e-13 * abs(float(r)) + 1e-300, (i, g, float(r))
