@@ -140,6 +140,15 @@ int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const
                               uint8_t* status_out, double* dP, double* dF, double* dK,
                               double* dT, const pivot_opts* opts, void* stream);
 
+/*
+ * pivot_mills_ratio -- Y(z) = Phi(z)/phi(z), the ratio through which the
+ * adjoint writes Delta/V (Eq. implicit_iv with F phi(d1) = K phi(d2)) and the
+ * normalised Black function writes b/b_s (Section 2, Eq. app_normalized_black).
+ *   in : z (n float64)   out: y (n float64)
+ * Exposed so that the FP64 erfcx behind it can be checked on its own.
+ */
+int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream);
+
 /* Human-readable text for a return code. */
 const char* pivot_error_string(int code);
 

@@ -29,6 +29,7 @@ _SIGNATURES = {
     "pivot_iv_backward": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp],
     "pivot_iv_forward_backward": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_vp, c_vp,
                                   c_vp, c_vp, c_vp, c_vp],
+    "pivot_mills_ratio": [c_i64, c_vp, c_vp, c_vp],
     "pivot_error_string": [ctypes.c_int],
     "pivot_version": [],
 }

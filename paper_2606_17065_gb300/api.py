@@ -106,6 +106,15 @@ def black_price_backward(F, K, T, sigma, flag, gbar=None):
     return tuple(_host_result((F, K, T, sigma, flag, gbar), outs))
 
 
+def mills_ratio(z):
+    """Y(z) = Phi(z)/phi(z) evaluated by the library's FP64 kernel."""
+    dev = _device_of(z)
+    zz = _on(z, dev, torch.float64)
+    y = torch.empty_like(zz)
+    _native.call("pivot_mills_ratio", zz.numel(), _p(zz), _p(y), _stream(dev))
+    return _host_result((z,), [y])[0]
+
+
 def _opts(mode, householder):
     o = _native.PivotOpts()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)

@@ -46,6 +46,13 @@ __global__ void __launch_bounds__(kBlock) k_black_price_backward(
   }
 }
 
+__global__ void __launch_bounds__(kBlock) k_mills_ratio(int64_t n, const double* __restrict__ z,
+                                                        double* __restrict__ y) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = pivot::mills_y<double>(z[i]);
+}
+
 __global__ void __launch_bounds__(kBlock) k_iv_backward(int64_t n, const double* __restrict__ F,
                                                         const double* __restrict__ K, const double* __restrict__ T,
                                                         const int8_t* __restrict__ flag,
@@ -488,6 +495,18 @@ int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const
   if (rc != PIVOT_OK) return rc;
   Args a{n, F, K, T, P, flag, gbar, tau, gate_mode, steps, sigma_out, status_out, dP, dF, dK, dT};
   return mode == PIVOT_MODE_MIXED ? launch_binned<true, true>(a, stream) : launch_binned<true, false>(a, stream);
+}
+
+int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream) {
+  if (n < 0) return PIVOT_E_SIZE;
+  if (n == 0) return PIVOT_OK;
+  int dev = -1;
+  const Ptr ps[] = {{z, true, true}, {y, true, true}};
+  int rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  k_mills_ratio<<<grid_for(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(n, z, y);
+  return launch_status();
 }
 
 const char* pivot_error_string(int code) {

@@ -51,13 +51,13 @@ def test_implied_vol_autograd_against_finite_differences(body):
     sig = pv.implied_volatility_autograd(Pt, to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(b.flag), 1e-6, "exact")
     sig.sum().backward()
     ad = to_np(Pt.grad)
-    h = 1e-6 * np.maximum(P, 1e-3)
-    up, _ = pv.iv(to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(P + h), to_dev(b.flag))
-    dn, _ = pv.iv(to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(P - h), to_dev(b.flag))
-    fd = (to_np(up) - to_np(dn)) / (2 * h)
+    h = 1e-4 * np.maximum(P, 1e-3)
+    f = lambda dp: to_np(pv.iv(to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(P + dp), to_dev(b.flag))[0])  # noqa
+    # fourth-order central difference (Richardson): truncation O(h^4), rounding ~ eps sigma / h
+    fd = (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h)
     rel = np.abs(fd[rows] - ad[rows]) / np.abs(ad[rows])
     assert rows.sum() > 1000
-    assert np.median(rel) < 1e-8 and rel.max() < 1e-5
+    assert np.median(rel) < 1e-10 and rel.max() < 1e-8
 
 
 def test_black_price_autograd_matches_oracle():

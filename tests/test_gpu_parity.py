@@ -291,3 +291,18 @@ def test_full_size_mixed_sampled():
     assert rel <= 2e-13, rel
     del F, K, T, flag, P_dev, sig, st, dP, dF, dK, dT, sig64, st64
     torch.cuda.empty_cache()
+
+
+def test_mills_ratio_fp64_erfcx():
+    """The library's FP64 erfcx (table + asymptotic series + reflection) through Y = Phi/phi,
+    against the oracle's quadrature Mills ratio."""
+    z = np.concatenate([np.linspace(-37.0, 37.0, 20001), -np.logspace(-12, 3, 400), np.logspace(-12, 1.5, 400),
+                        [0.0, -0.0, np.inf, -np.inf]])
+    y = to_np(pv.api.mills_ratio(to_dev(z)))
+    ref = np.array([oracle.mills(v) for v in z])
+    fin = np.isfinite(ref) & (ref > 0)
+    # conditioning of Y in z: |z Y'/Y| ~ z^2 for z > 0 (exp(z^2/2) growth)
+    tol = 8 * EPS * (1 + np.where(z > 0, z * z, 0.0))
+    rel = np.abs(y[fin] - ref[fin]) / ref[fin]
+    assert np.all(rel <= tol[fin]), rel.max()
+    assert y[z == -np.inf][0] == 0.0 and np.isinf(y[z == np.inf][0])
