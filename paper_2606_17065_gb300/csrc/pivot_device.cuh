@@ -89,7 +89,7 @@ __device__ __forceinline__ double erfcx_fp64(double a) {
   if (a < 0.0) {
     const double p = a * a, e = fma(a, a, -p); // a^2 = p + e exactly
     const double ex = 2.0 * exp(p);
-    r = fma(ex, e, ex) - r;
+    r = (p < 709.0) ? fma(ex, e, ex) - r : INFINITY;
   }
   return r;
 }

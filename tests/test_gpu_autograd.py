@@ -51,7 +51,8 @@ def test_implied_vol_autograd_against_finite_differences(body):
     sig = pv.implied_volatility_autograd(Pt, to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(b.flag), 1e-6, "exact")
     sig.sum().backward()
     ad = to_np(Pt.grad)
-    h = 1e-4 * np.maximum(P, 1e-3)
+    itm = np.where(b.flag > 0, np.maximum(b.F - b.K, 0), np.maximum(b.K - b.F, 0))
+    h = 1e-4 * (P - itm)  # steps scale with the time value, so P +- 2h stays inside (intrinsic, upper)
     f = lambda dp: to_np(pv.iv(to_dev(b.F), to_dev(b.K), to_dev(b.T), to_dev(P + dp), to_dev(b.flag))[0])  # noqa
     # fourth-order central difference (Richardson): truncation O(h^4), rounding ~ eps sigma / h
     fd = (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h)
