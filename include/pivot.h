@@ -45,6 +45,7 @@ extern "C" {
 #define PIVOT_E_OPTS 4        /* bad pivot_opts field */
 #define PIVOT_E_NOT_DEVICE 5  /* a pointer is not accessible from the current device */
 #define PIVOT_E_ALIGN 6       /* a float64 pointer is not 8-byte aligned */
+#define PIVOT_E_MLP 7         /* PIVOT_MODE_LEARNED without weights, or bad training hyper-parameters */
 
 /* ---- per-row status codes (uint8) --------------------------------------- */
 #define PIVOT_ROW_OK 0              /* sigma finite and > 0 */
@@ -61,12 +62,48 @@ extern "C" {
 #define PIVOT_GATE_SMOOTH 3 /* every row times w_tau(V) = V^2 / (V^2 + tau^2) */
 
 /* ---- forward variants ----------------------------------------------------- */
-#define PIVOT_MODE_FP64 0   /* plain FP64 throughout */
-#define PIVOT_MODE_MIXED 1  /* FP32 guess and first Householder step, FP64 final step */
+#define PIVOT_MODE_FP64 0    /* plain FP64 throughout */
+#define PIVOT_MODE_MIXED 1   /* FP32 guess and first Householder step, FP64 final step */
+#define PIVOT_MODE_LEARNED 2 /* MLP initial guess (BF16 tensor cores), FP64 Householder steps */
+
+/* ---- learned initial guess ------------------------------------------------
+ * An MLP 2 -> 64 -> 64 -> 64 -> 1 (SiLU) maps (|x|, q = 1/sqrt(-2 ln beta))
+ * to ln(s / s_a), s_a = |x| q + sqrt(2 pi) beta, for the out-of-the-money
+ * normalised problem b(x, s) = beta.  Weights are BF16 (bit patterns in
+ * uint16), biases FP32, accumulation FP32.  Flat FP32 parameter order:
+ * w1[64][2], b1[64], w2[64][64], b2[64], w3[64][64], b3[64], w4[64], b4
+ * (w[unit][input]).  Not in the paper: the paper keeps LBR's rational seed;
+ * this is the surrogate seed the build adds and measures against it. */
+#define PIVOT_MLP_HIDDEN 64
+#define PIVOT_MLP_NPARAM 8577
 
 typedef struct {
-  int32_t mode;        /* PIVOT_MODE_* ; default PIVOT_MODE_FP64 */
-  int32_t householder; /* Householder(3) iterations after the initial guess, 0 = default (2), max 4 */
+  uint16_t w1[64 * 2];  /* bf16 [unit][input] */
+  uint16_t w2[64 * 64]; /* bf16 [unit][input] */
+  uint16_t w3[64 * 64]; /* bf16 [unit][input] */
+  uint16_t w4[64];      /* bf16 */
+  float b1[64], b2[64], b3[64];
+  float b4;
+  float reserved[3];
+} pivot_mlp; /* inference weights, device memory */
+
+typedef struct {
+  float param[PIVOT_MLP_NPARAM]; /* FP32 master parameters (flat order above) */
+  float grad[PIVOT_MLP_NPARAM];  /* gradient accumulator (zeroed by pivot_mlp_adam) */
+  float adam_m[PIVOT_MLP_NPARAM];
+  float adam_v[PIVOT_MLP_NPARAM];
+  double loss_sum; /* sum of squared errors accumulated by pivot_mlp_grad */
+  double rows;     /* rows that entered loss_sum */
+  int64_t step;    /* Adam steps taken */
+  pivot_mlp net;   /* BF16 copy of the parameters, refreshed by pivot_mlp_init / pivot_mlp_adam */
+} pivot_mlp_trainer; /* training state, device memory owned by the caller */
+
+typedef struct {
+  int32_t mode;          /* PIVOT_MODE_* ; default PIVOT_MODE_FP64 */
+  int32_t householder;   /* Householder(3) iterations after the initial guess, 0 = default (2), max 4 */
+  const pivot_mlp* mlp;  /* PIVOT_MODE_LEARNED: device pointer to the weights, else ignored */
+  double fallback;       /* PIVOT_MODE_LEARNED: a first Householder correction |ds|/s above this sends
+                            the row to the rational-guess path; 0 = default 1e-2 */
 } pivot_opts;
 
 /*
@@ -148,6 +185,42 @@ int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const
  * Exposed so that the FP64 erfcx behind it can be checked on its own.
  */
 int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream);
+
+/*
+ * Training of the learned initial guess with the library's own kernels
+ * (BF16 tensor-core forward and backward, FP32 accumulation).  The training
+ * pairs are the operator's own: quotes (F, K, T, P, flag) and the sigma that
+ * pivot_iv_forward returned for them; rows whose sigma is not finite and > 0
+ * are skipped.  Loss: mean over the rows of (MLP(|x|, q) - ln(s / s_a))^2.
+ *
+ * pivot_mlp_init  -- parameters uniform in +-1/sqrt(fan_in) from `seed`
+ *                    (counter-based), moments and gradient zeroed, BF16 copy written.
+ * pivot_mlp_grad  -- adds d(sum of squared errors)/d(param) over n rows to
+ *                    trainer->grad and the loss to trainer->loss_sum / rows.
+ * pivot_mlp_adam  -- one Adam step on trainer->param with grad / rows (mean
+ *                    loss), then zeroes grad, loss_sum and rows and refreshes
+ *                    trainer->net.
+ * The trainer must not be used by two calls that overlap on the GPU.
+ */
+int pivot_mlp_init(pivot_mlp_trainer* trainer, uint64_t seed, void* stream);
+int pivot_mlp_grad(pivot_mlp_trainer* trainer, int64_t n, const double* F, const double* K,
+                   const double* T, const double* P, const int8_t* flag, const double* sigma,
+                   void* stream);
+int pivot_mlp_adam(pivot_mlp_trainer* trainer, double lr, double beta1, double beta2, double eps,
+                   void* stream);
+
+/* sizeof(pivot_mlp_trainer) and offsetof(pivot_mlp_trainer, net), for bindings. */
+int64_t pivot_mlp_trainer_bytes(int64_t* net_offset);
+
+/*
+ * pivot_iv_guess -- the initial guess s^(0) alone (before any Householder
+ * step), for measuring seeds against the root: opts NULL or PIVOT_MODE_FP64
+ * gives LBR's four-region rational guess (appendix stage 4), PIVOT_MODE_LEARNED
+ * the MLP seed.  Rows that need no solve get NaN.
+ *   in : F, K, T, P (n float64), flag (n int8)   out: s_out (n float64)
+ */
+int pivot_iv_guess(int64_t n, const double* F, const double* K, const double* T, const double* P,
+                   const int8_t* flag, const pivot_opts* opts, double* s_out, void* stream);
 
 /* Human-readable text for a return code. */
 const char* pivot_error_string(int code);

@@ -19,7 +19,8 @@ c_i64, c_i32, c_dbl, c_vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, cty
 
 
 class PivotOpts(ctypes.Structure):
-    _fields_ = [("mode", ctypes.c_int32), ("householder", ctypes.c_int32)]
+    _fields_ = [("mode", ctypes.c_int32), ("householder", ctypes.c_int32), ("mlp", ctypes.c_void_p),
+                ("fallback", ctypes.c_double)]
 
 
 _SIGNATURES = {
@@ -30,6 +31,11 @@ _SIGNATURES = {
     "pivot_iv_forward_backward": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_vp, c_vp,
                                   c_vp, c_vp, c_vp, c_vp],
     "pivot_mills_ratio": [c_i64, c_vp, c_vp, c_vp],
+    "pivot_mlp_trainer_bytes": [c_vp],
+    "pivot_iv_guess": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
+    "pivot_mlp_init": [c_vp, ctypes.c_uint64, c_vp],
+    "pivot_mlp_grad": [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
+    "pivot_mlp_adam": [c_vp, c_dbl, c_dbl, c_dbl, c_dbl, c_vp],
     "pivot_error_string": [ctypes.c_int],
     "pivot_version": [],
 }
@@ -67,6 +73,7 @@ def lib():
             fn.argtypes = args
             fn.restype = ctypes.c_int
         handle.pivot_error_string.restype = ctypes.c_char_p
+        handle.pivot_mlp_trainer_bytes.restype = ctypes.c_int64
         _lib = handle
         return _lib
 

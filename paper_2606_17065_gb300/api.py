@@ -16,7 +16,7 @@ from . import _native
 
 ROW_OK, ROW_BELOW_INTRINSIC, ROW_ABOVE_UPPER, ROW_BAD_INPUT, ROW_AT_INTRINSIC, ROW_AT_UPPER = range(6)
 GATES = {"exact": 0, "nan": 1, "mask": 2, "smooth": 3}
-MODES = {"fp64": 0, "mixed": 1}
+MODES = {"fp64": 0, "mixed": 1, "learned": 2}
 
 
 def _gate(gate) -> int:
@@ -115,14 +115,74 @@ def mills_ratio(z):
     return _host_result((z,), [y])[0]
 
 
-def _opts(mode, householder):
+def _opts(mode, householder, mlp=None, fallback: float = 0.0):
     o = _native.PivotOpts()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.householder = int(householder)
+    o.mlp = None if mlp is None else mlp.weights_ptr()
+    o.fallback = float(fallback)
     return o
 
 
-def iv(F, K, T, P, flag, *, mode="fp64", householder: int = 0, status: bool = True):
+class MlpTrainer:
+    """Device state of the learned initial guess (pivot_mlp_trainer in include/pivot.h).
+
+    ``init``, ``grad`` and ``adam`` run the library's own kernels; ``weights_ptr``
+    is what PIVOT_MODE_LEARNED reads.
+    """
+
+    def __init__(self, device=None, seed: int = 0):
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        off = ctypes.c_int64(0)
+        nbytes = _native.lib().pivot_mlp_trainer_bytes(ctypes.byref(off))
+        self.net_offset = int(off.value)
+        self.buf = torch.zeros(int(nbytes), dtype=torch.uint8, device=self.device)
+        self.init(seed)
+
+    def ptr(self):
+        return ctypes.c_void_p(self.buf.data_ptr())
+
+    def weights_ptr(self):
+        return self.buf.data_ptr() + self.net_offset
+
+    def init(self, seed: int = 0):
+        _native.call("pivot_mlp_init", self.ptr(), ctypes.c_uint64(seed), _stream(self.device))
+
+    def grad(self, F, K, T, P, flag, sigma):
+        """Accumulate the gradient of sum (MLP - ln(s/s_a))^2 over the rows (the operator's own pairs)."""
+        f, k, t, p, s = (_on(a, self.device, torch.float64) for a in (F, K, T, P, sigma))
+        fl = _on(flag, self.device, torch.int8)
+        _native.call("pivot_mlp_grad", self.ptr(), f.numel(), _p(f), _p(k), _p(t), _p(p), _p(fl), _p(s),
+                     _stream(self.device))
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        _native.call("pivot_mlp_adam", self.ptr(), float(lr), float(beta1), float(beta2), float(eps),
+                     _stream(self.device))
+
+    def fields(self):
+        """(param, grad, loss_sum, rows, step) read back from the device (a synchronising copy)."""
+        n = 8577
+        f32 = self.buf[: 4 * 4 * n].view(torch.float32)
+        tail = self.buf[4 * 4 * n: 4 * 4 * n + 24]
+        d = tail[:16].view(torch.float64).cpu()
+        step = int(tail[16:24].view(torch.int64).cpu()[0])
+        return f32[:n].clone(), f32[n:2 * n].clone(), float(d[0]), float(d[1]), step
+
+
+def iv_guess(F, K, T, P, flag, *, mode="fp64", mlp=None):
+    """The initial guess s^(0) alone: LBR's rational seed (fp64) or the MLP seed (learned)."""
+    dev = _device_of(F, K, T, P, flag)
+    f, k, t, p = (_on(a, dev, torch.float64) for a in (F, K, T, P))
+    fl = _on(flag, dev, torch.int8)
+    n = f.numel()
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    o = _opts(mode, 0, mlp)
+    _native.call("pivot_iv_guess", n, _p(f), _p(k), _p(t), _p(p), _p(fl), ctypes.byref(o), _p(out), _stream(dev))
+    return _host_result((F, K, T, P, flag), [out])[0]
+
+
+def iv(F, K, T, P, flag, *, mode="fp64", householder: int = 0, status: bool = True, mlp=None,
+       fallback: float = 0.0):
     """Implied volatility (Algorithm 1 forward); returns (sigma, status or None)."""
     dev = _device_of(F, K, T, P, flag)
     f, k, t, p = (_on(a, dev, torch.float64) for a in (F, K, T, P))
@@ -131,7 +191,7 @@ def iv(F, K, T, P, flag, *, mode="fp64", householder: int = 0, status: bool = Tr
     _check_lengths(n, k, t, p, fl)
     sig = torch.empty(n, dtype=torch.float64, device=dev)
     st = torch.empty(n, dtype=torch.uint8, device=dev) if status else None
-    o = _opts(mode, householder)
+    o = _opts(mode, householder, mlp, fallback)
     _native.call("pivot_iv_forward", n, _p(f), _p(k), _p(t), _p(p), _p(fl), _p(sig), _p(st), ctypes.byref(o),
                  _stream(dev))
     return tuple(_host_result((F, K, T, P, flag), [sig, st]))
@@ -152,7 +212,7 @@ def iv_backward(F, K, T, flag, sigma, gbar=None, *, tau: float = 1e-6, gate="nan
 
 
 def iv_forward_backward(F, K, T, P, flag, gbar=None, *, tau: float = 1e-6, gate="nan", mode="fp64",
-                        householder: int = 0):
+                        householder: int = 0, mlp=None, fallback: float = 0.0):
     """Forward and gated adjoint in one pass; returns (sigma, status, dP, dF, dK, dT)."""
     dev = _device_of(F, K, T, P, flag, gbar)
     f, k, t, p = (_on(a, dev, torch.float64) for a in (F, K, T, P))
@@ -163,7 +223,7 @@ def iv_forward_backward(F, K, T, P, flag, gbar=None, *, tau: float = 1e-6, gate=
     sig = torch.empty(n, dtype=torch.float64, device=dev)
     st = torch.empty(n, dtype=torch.uint8, device=dev)
     outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
-    o = _opts(mode, householder)
+    o = _opts(mode, householder, mlp, fallback)
     _native.call("pivot_iv_forward_backward", n, _p(f), _p(k), _p(t), _p(p), _p(fl), _p(g), float(tau),
                  _gate(gate), _p(sig), _p(st), *[_p(x) for x in outs], ctypes.byref(o), _stream(dev))
     return tuple(_host_result((F, K, T, P, flag, gbar), [sig, st, *outs]))

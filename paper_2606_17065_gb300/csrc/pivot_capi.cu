@@ -11,11 +11,11 @@
 
 #include "pivot.h"
 #include "pivot_device.cuh"
+#include "pivot_internal.cuh"
 
 namespace {
 
-constexpr int kBlock = 256;
-constexpr int kDefaultSteps = 2;
+using namespace pivot::detail;
 
 __global__ void __launch_bounds__(kBlock) k_black_price(int64_t n, const double* __restrict__ F,
                                                         const double* __restrict__ K, const double* __restrict__ T,
@@ -96,41 +96,6 @@ constexpr int kBins = 8;
 constexpr double kMixedFloor = 1e-30;
 constexpr double kMixedMaxAbsX = 80.0;
 constexpr size_t kBinnedSmem = size_t(kNodeFields) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
-
-struct Args {
-  int64_t n;
-  const double *F, *K, *T, *P;
-  const int8_t* flag;
-  const double* gbar;
-  double tau;
-  int mode;
-  int steps;
-  double* sigma;
-  uint8_t* status;
-  double *dP, *dF, *dK, *dT;
-};
-
-__device__ __forceinline__ void write_grad(const Args& a, int64_t i, double F, double K, double T, int fl,
-                                           double sig) {
-  const double g = a.gbar ? a.gbar[i] : 1.0;
-  const pivot::Grad d = pivot::gated_adjoint(F, K, T, fl, sig, g, a.tau, a.mode);
-  if (a.dP) a.dP[i] = d.dP;
-  if (a.dF) a.dF[i] = d.dF;
-  if (a.dK) a.dK[i] = d.dK;
-  if (a.dT) a.dT[i] = d.dT;
-}
-
-// warp-aggregated append: returns this lane's slot in a shared counter
-__device__ __forceinline__ int warp_append(bool take, int* counter, int lane) {
-  const unsigned m = __ballot_sync(0xffffffffu, take);
-  int b0 = 0;
-  if (m) {
-    const int leader = __ffs(m) - 1;
-    if (lane == leader) b0 = atomicAdd(counter, __popc(m));
-    b0 = __shfl_sync(0xffffffffu, b0, leader);
-  }
-  return b0 + __popc(m & ((1u << lane) - 1u));
-}
 
 template <bool kBackward, bool kMixed>
 __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
@@ -302,72 +267,19 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// host-side argument checks
-// ---------------------------------------------------------------------------
-int check_ptr(const void* p, bool required, bool f64, int* device) {
-  if (p == nullptr) return required ? PIVOT_E_NULL : PIVOT_OK;
-  if (f64 && (reinterpret_cast<uintptr_t>(p) & 7u)) return PIVOT_E_ALIGN;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return PIVOT_E_NOT_DEVICE;
-  }
-  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return PIVOT_E_NOT_DEVICE;
-  if (*device < 0) *device = a.device;
-  else if (a.device != *device) return PIVOT_E_NOT_DEVICE;
-  return PIVOT_OK;
-}
-
-struct Ptr {
-  const void* p;
-  bool required;
-  bool f64;
-};
-
-template <int N>
-int check_all(const Ptr (&ps)[N], int* device) {
-  for (int i = 0; i < N; ++i) {
-    const int rc = check_ptr(ps[i].p, ps[i].required, ps[i].f64, device);
-    if (rc != PIVOT_OK) return rc;
-  }
-  return PIVOT_OK;
-}
-
-int check_gate(double tau, int32_t mode) {
-  if (mode < PIVOT_GATE_EXACT || mode > PIVOT_GATE_SMOOTH) return PIVOT_E_GATE;
-  if (!(tau >= 0.0) || !(tau < INFINITY)) return PIVOT_E_GATE;
-  if (mode == PIVOT_GATE_SMOOTH && !(tau > 0.0)) return PIVOT_E_GATE;
-  return PIVOT_OK;
-}
-
 int check_opts(const pivot_opts* o, int* steps, int* mode) {
   *steps = kDefaultSteps;
   *mode = PIVOT_MODE_FP64;
   if (o == nullptr) return PIVOT_OK;
-  if (o->mode != PIVOT_MODE_FP64 && o->mode != PIVOT_MODE_MIXED) return PIVOT_E_OPTS;
+  if (o->mode != PIVOT_MODE_FP64 && o->mode != PIVOT_MODE_MIXED && o->mode != PIVOT_MODE_LEARNED)
+    return PIVOT_E_OPTS;
   if (o->householder < 0 || o->householder > 4) return PIVOT_E_OPTS;
+  if (o->mode == PIVOT_MODE_LEARNED) {
+    if (o->mlp == nullptr) return PIVOT_E_MLP;
+    if (!(o->fallback >= 0.0) || !(o->fallback < 1.0)) return PIVOT_E_MLP;
+  }
   if (o->householder > 0) *steps = o->householder;
   *mode = o->mode;
-  return PIVOT_OK;
-}
-
-unsigned grid_for(int64_t n) {
-  const int64_t blocks = (n + kBlock - 1) / kBlock;
-  const int64_t cap = int64_t(1) << 20;
-  return unsigned(blocks < cap ? blocks : cap);
-}
-
-int launch_status() {
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? PIVOT_OK : -int(e);
-}
-
-int select_device(int device) {
-  if (device < 0) return PIVOT_OK;
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess) return PIVOT_E_NOT_DEVICE;
-  if (cur != device && cudaSetDevice(device) != cudaSuccess) return PIVOT_E_NOT_DEVICE;
   return PIVOT_OK;
 }
 
@@ -453,6 +365,12 @@ int pivot_iv_forward(int64_t n, const double* F, const double* K, const double* 
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
   Args a{n, F, K, T, P, flag, nullptr, 0.0, 0, steps, sigma_out, status_out, nullptr, nullptr, nullptr, nullptr};
+  if (mode == PIVOT_MODE_LEARNED) {
+    int d2 = dev;
+    rc = check_ptr(opts->mlp, true, true, &d2);
+    if (rc != PIVOT_OK) return rc;
+    return launch_learned(a, opts->mlp, opts->fallback, false, stream);
+  }
   return mode == PIVOT_MODE_MIXED ? launch_binned<false, true>(a, stream) : launch_binned<false, false>(a, stream);
 }
 
@@ -494,6 +412,12 @@ int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
   Args a{n, F, K, T, P, flag, gbar, tau, gate_mode, steps, sigma_out, status_out, dP, dF, dK, dT};
+  if (mode == PIVOT_MODE_LEARNED) {
+    int d2 = dev;
+    rc = check_ptr(opts->mlp, true, true, &d2);
+    if (rc != PIVOT_OK) return rc;
+    return launch_learned(a, opts->mlp, opts->fallback, true, stream);
+  }
   return mode == PIVOT_MODE_MIXED ? launch_binned<true, true>(a, stream) : launch_binned<true, false>(a, stream);
 }
 
@@ -518,6 +442,7 @@ const char* pivot_error_string(int code) {
     case PIVOT_E_OPTS: return "bad pivot_opts";
     case PIVOT_E_NOT_DEVICE: return "a pointer is not device memory of the current device";
     case PIVOT_E_ALIGN: return "a float64 pointer is not 8-byte aligned";
+    case PIVOT_E_MLP: return "learned mode without weights, or bad training hyper-parameters";
     default: break;
   }
   if (code < 0) return cudaGetErrorString(static_cast<cudaError_t>(-code));

@@ -1,0 +1,470 @@
+// pivot_learned.cu -- PIVOT_MODE_LEARNED: the MLP initial guess on BF16 tensor
+// cores (mma.sync, FP32 accumulation), FP64 Householder(3) steps on the LBR
+// objectives (appendix stage 5), the gated adjoint, and the training kernels
+// of the MLP (forward, backward and Adam, all in this file).
+#include <cstddef>
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "pivot.h"
+#include "pivot_device.cuh"
+#include "pivot_internal.cuh"
+#include "pivot_mlp.cuh"
+
+namespace {
+
+using namespace pivot::detail;
+namespace M = pivot::mlp;
+
+constexpr int kLBlock = 128; // 4 warps
+constexpr int kLWarps = kLBlock / 32;
+constexpr int kLTile = 512;
+constexpr int kLRowsPerThread = kLTile / kLBlock;
+constexpr double kDefaultFallback = 1e-2;
+
+struct LearnedSmem {
+  M::Weights W;
+  __nv_bfloat16 tiles[kLWarps][2][M::kRows * M::LDA];
+  double x[kLTile], bmax[kLTile], bb[kLTile], lnb[kLTile], s0[kLTile];
+  uint16_t list[kLTile], order[kLTile], pos[kLTile];
+  uint8_t bin[kLTile];
+  int nsolve, cnt[2], off[3];
+};
+
+// The quote's normalised problem and its MLP features (lane = row); `has`
+// false gives neutral features for the lanes that only keep the warp full.
+struct LearnedRow {
+  double x, bmax, beta, betac, lnb;
+  M::Features f;
+};
+
+__device__ __forceinline__ LearnedRow learned_row(double F, double K, double T, double P, int fl) {
+  LearnedRow r;
+  const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
+  pivot::moneyness(F, K, r.x, r.bmax);
+  const double rsq = rsqrt(F * K);
+  r.beta = q.tv * rsq;
+  r.betac = q.cv * rsq;
+  r.lnb = pivot::log_beta(r.beta, F, K, T, P, fl);
+  r.f = M::features(r.x, r.beta, r.lnb);
+  return r;
+}
+
+template <bool kBackward>
+__global__ void __launch_bounds__(kLBlock, 2) k_iv_learned(Args a, const pivot_mlp* net, double fallback) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LearnedSmem& S = *reinterpret_cast<LearnedSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  M::stage_weights(net, S.W, nullptr);
+  __syncthreads();
+  for (int64_t base = int64_t(blockIdx.x) * kLTile; base < a.n; base += int64_t(gridDim.x) * kLTile) {
+    if (tid == 0) {
+      S.nsolve = 0;
+      S.cnt[0] = S.cnt[1] = 0;
+    }
+    __syncthreads();
+    // ---- phase 1: finish rows that need no solve, list the others
+#pragma unroll
+    for (int j = 0; j < kLRowsPerThread; ++j) {
+      const int r = j * kLBlock + tid;
+      const int64_t i = base + r;
+      bool solve = false;
+      if (i < a.n) {
+        const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
+        const int fl = a.flag[i];
+        const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
+        if (q.status != 0) {
+          a.sigma[i] = q.sigma;
+          if (a.status) a.status[i] = uint8_t(q.status);
+          if (kBackward) write_grad(a, i, F, K, T, fl, q.sigma);
+        } else {
+          solve = true;
+        }
+      }
+      const int slot = warp_append(solve, &S.nsolve, lane);
+      if (solve) S.list[slot] = uint16_t(r);
+    }
+    __syncthreads();
+    // ---- phase 2: MLP seed for the listed rows, 32 per warp; side of the inflection
+    const int nsolve = S.nsolve;
+    for (int c = warp; c * 32 < nsolve; c += kLWarps) {
+      const int qi = c * 32 + lane;
+      const bool has = qi < nsolve;
+      const int r = has ? S.list[qi] : 0;
+      LearnedRow row;
+      float f0 = 0.0f, f1 = 0.5f;
+      if (has) {
+        const int64_t i = base + r;
+        row = learned_row(a.F[i], a.K[i], a.T[i], a.P[i], a.flag[i]);
+        f0 = row.f.f0;
+        f1 = row.f.f1;
+      }
+      const float o = M::forward_warp(f0, f1, S.W, S.tiles[warp][0], S.tiles[warp][1]);
+      int bin = -1;
+      if (has) {
+        const double e = pivot::erfcx_fp64(sqrt(-row.x));
+        const bool low = row.beta <= 0.5 * row.bmax * (1.0 - e);
+        bin = low ? 0 : 1;
+        S.x[r] = row.x;
+        S.bmax[r] = row.bmax;
+        S.bb[r] = low ? row.beta : row.betac;
+        S.lnb[r] = row.lnb;
+        S.s0[r] = row.f.sa * exp(double(o));
+        S.bin[r] = uint8_t(bin);
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int p = warp_append(bin == k, &S.cnt[k], lane);
+        if (bin == k) S.pos[r] = uint16_t(p);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      S.off[0] = 0;
+      S.off[1] = S.cnt[0];
+      S.off[2] = S.cnt[0] + S.cnt[1];
+    }
+    __syncthreads();
+    for (int qi = tid; qi < nsolve; qi += kLBlock) {
+      const int r = S.list[qi];
+      S.order[S.off[S.bin[r]] + S.pos[r]] = uint16_t(r);
+    }
+    __syncthreads();
+    // ---- phase 3: FP64 Householder steps from the seed, side after side
+    const int total = S.off[2];
+    for (int qi = tid; qi < total; qi += kLBlock) {
+      const int r = S.order[qi];
+      const bool up = qi >= S.off[1];
+      const int rg = up ? pivot::kUpper : pivot::kLower;
+      const int64_t i = base + r;
+      const double F = a.F[i], K = a.K[i], T = a.T[i];
+      const int fl = a.flag[i];
+      const double x = S.x[r], bb = S.bb[r];
+      const double lnbetac = up ? log(bb) : 0.0;
+      const double inv_lnbeta = up ? 0.0 : 1.0 / S.lnb[r];
+      double s = S.s0[r];
+      bool ok = s > 0.0 && s < INFINITY;
+      if (ok) {
+        const double s1 = pivot::householder_step<double>(x, bb, lnbetac, inv_lnbeta, rg, s);
+        ok = s1 > 0.0 && s1 < INFINITY && fabs(s1 - s) <= fallback * s1;
+        s = s1;
+        for (int k = 1; ok && k < a.steps; ++k) s = pivot::householder_step<double>(x, bb, lnbetac, inv_lnbeta, rg, s);
+      }
+      if (!ok) {
+        // the seed is outside its trust region: LBR's rational guess and the FP64 path
+        const pivot::Quote q = pivot::classify_quote(F, K, T, a.P[i], fl);
+        double x2, bmax2;
+        pivot::moneyness(F, K, x2, bmax2);
+        const double rsq = rsqrt(F * K);
+        pivot::Node<double> nd;
+        const int rg2 = pivot::classify<double>(x2, bmax2, q.tv * rsq, q.cv * rsq, nd);
+        const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, a.P[i], fl) : 0.0;
+        s = pivot::solve_region<double>(rg2, nd, lnb2, a.steps);
+      }
+      const double inv_sqT = rsqrt(T);
+      const double sig = s * inv_sqT;
+      a.sigma[i] = sig;
+      if (a.status) a.status[i] = 0;
+      if (kBackward) {
+        const double g = a.gbar ? a.gbar[i] : 1.0;
+        const double xs = (F >= K) ? -x : x;
+        const pivot::Grad d = isnan(g) ? pivot::degenerate_grad(true, g, a.mode)
+                                       : pivot::adjoint_core(F, K, fl, sig, s, xs, inv_sqT, rsqrt(F * K), g,
+                                                             a.tau, a.mode);
+        if (a.dP) a.dP[i] = d.dP;
+        if (a.dF) a.dF[i] = d.dF;
+        if (a.dK) a.dK[i] = d.dK;
+        if (a.dT) a.dT[i] = d.dT;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial guesses alone (diagnostics: how far each seed is from the root).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_guess_rational(int64_t n, const double* __restrict__ F,
+                                                           const double* __restrict__ K, const double* __restrict__ T,
+                                                           const double* __restrict__ P, const int8_t* __restrict__ flag,
+                                                           double* __restrict__ s_out) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const pivot::Quote q = pivot::classify_quote(F[i], K[i], T[i], P[i], flag[i]);
+    double s = __longlong_as_double(0x7ff8000000000000LL);
+    if (q.status == 0) {
+      double x, bmax;
+      pivot::moneyness(F[i], K[i], x, bmax);
+      const double rsq = rsqrt(F[i] * K[i]);
+      pivot::Node<double> nd;
+      const int rg = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
+      const double lnb = (rg == pivot::kLower) ? pivot::log_beta(nd.bb, F[i], K[i], T[i], P[i], flag[i]) : 0.0;
+      s = pivot::region_guess<double>(rg, nd, lnb);
+    }
+    s_out[i] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kLBlock) k_guess_mlp(int64_t n, const double* __restrict__ F,
+                                                       const double* __restrict__ K, const double* __restrict__ T,
+                                                       const double* __restrict__ P, const int8_t* __restrict__ flag,
+                                                       const pivot_mlp* net, double* __restrict__ s_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  M::Weights& W = *reinterpret_cast<M::Weights*>(smem_raw);
+  __nv_bfloat16* tiles = reinterpret_cast<__nv_bfloat16*>(smem_raw + ((sizeof(M::Weights) + 15) / 16) * 16);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  M::stage_weights(net, W, nullptr);
+  __syncthreads();
+  __nv_bfloat16* RA = tiles + warp * 2 * M::kRows * M::LDA;
+  __nv_bfloat16* RB = RA + M::kRows * M::LDA;
+  for (int64_t c0 = (int64_t(blockIdx.x) * kLWarps + warp) * 32; c0 < n; c0 += int64_t(gridDim.x) * kLWarps * 32) {
+    const int64_t i = c0 + lane;
+    bool has = false;
+    LearnedRow row;
+    float f0 = 0.0f, f1 = 0.5f;
+    if (i < n) {
+      const pivot::Quote q = pivot::classify_quote(F[i], K[i], T[i], P[i], flag[i]);
+      if (q.status == 0) {
+        has = true;
+        row = learned_row(F[i], K[i], T[i], P[i], flag[i]);
+        f0 = row.f.f0;
+        f1 = row.f.f1;
+      }
+    }
+    const float o = M::forward_warp(f0, f1, W, RA, RB);
+    if (i < n) s_out[i] = has ? row.f.sa * exp(double(o)) : __longlong_as_double(0x7ff8000000000000LL);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Training: parameters, gradient pass, Adam.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ void write_net_param(pivot_mlp* net, int i, float p) {
+  const uint16_t b = __bfloat16_as_ushort(__float2bfloat16_rn(p));
+  if (i < M::OB1) net->w1[i - M::OW1] = b;
+  else if (i < M::OW2) net->b1[i - M::OB1] = p;
+  else if (i < M::OB2) net->w2[i - M::OW2] = b;
+  else if (i < M::OW3) net->b2[i - M::OB2] = p;
+  else if (i < M::OB3) net->w3[i - M::OW3] = b;
+  else if (i < M::OW4) net->b3[i - M::OB3] = p;
+  else if (i < M::OB4) net->w4[i - M::OW4] = b;
+  else net->b4 = p;
+}
+
+__global__ void k_mlp_init(pivot_mlp_trainer* tr, uint64_t seed) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M::NPARAM; i += gridDim.x * blockDim.x) {
+    const int fan_in = (i < M::OW2) ? 2 : M::H;
+    const double u = double(splitmix64(seed * 0x100000001B3ull + uint64_t(i)) >> 11) * (1.0 / 9007199254740992.0);
+    const float p = float((2.0 * u - 1.0) * rsqrt(double(fan_in)));
+    tr->param[i] = p;
+    tr->grad[i] = 0.0f;
+    tr->adam_m[i] = 0.0f;
+    tr->adam_v[i] = 0.0f;
+    write_net_param(&tr->net, i, p);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    tr->loss_sum = 0.0;
+    tr->rows = 0.0;
+    tr->step = 0;
+  }
+}
+
+struct TrainSmem {
+  M::Weights W;
+  M::WeightsT WT;
+  M::TrainTiles tiles[kLWarps];
+};
+
+__global__ void __launch_bounds__(kLBlock, 1) k_mlp_grad(pivot_mlp_trainer* tr, int64_t n, const double* __restrict__ F,
+                                                         const double* __restrict__ K, const double* __restrict__ T,
+                                                         const double* __restrict__ P, const int8_t* __restrict__ flag,
+                                                         const double* __restrict__ sigma) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  M::stage_weights(&tr->net, S.W, &S.WT);
+  __syncthreads();
+  float sq = 0.0f;
+  int nvalid = 0;
+  for (int64_t c0 = (int64_t(blockIdx.x) * kLWarps + warp) * 32; c0 < n; c0 += int64_t(gridDim.x) * kLWarps * 32) {
+    const int64_t i = c0 + lane;
+    bool valid = false;
+    float f0 = 0.0f, f1 = 0.5f, y = 0.0f;
+    if (i < n) {
+      const double sg = sigma[i];
+      const pivot::Quote q = pivot::classify_quote(F[i], K[i], T[i], P[i], flag[i]);
+      if (q.status == 0 && sg > 0.0 && sg < INFINITY) {
+        const LearnedRow row = learned_row(F[i], K[i], T[i], P[i], flag[i]);
+        const double target = log(sg * sqrt(T[i]) / row.f.sa);
+        if (row.f.sa > 0.0 && fabs(target) < 1e30) {
+          valid = true;
+          f0 = row.f.f0;
+          f1 = row.f.f1;
+          y = float(target);
+        }
+      }
+    }
+    sq += M::train_warp(f0, f1, y, valid, S.W, S.WT, S.tiles[warp], tr->grad);
+    nvalid += valid ? 1 : 0;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    nvalid += __shfl_xor_sync(0xffffffffu, nvalid, off);
+  }
+  if (lane == 0) {
+    atomicAdd(&tr->loss_sum, double(sq));
+    atomicAdd(&tr->rows, double(nvalid));
+  }
+}
+
+__global__ void k_mlp_adam(pivot_mlp_trainer* tr, double lr, double beta1, double beta2, double eps) {
+  const double rows = tr->rows;
+  const double inv = rows > 0.0 ? 1.0 / rows : 0.0;
+  const double t = double(tr->step + 1);
+  const double c1 = 1.0 / (1.0 - pow(beta1, t)), c2 = 1.0 / (1.0 - pow(beta2, t));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M::NPARAM; i += gridDim.x * blockDim.x) {
+    const double g = double(tr->grad[i]) * inv;
+    const double m = beta1 * double(tr->adam_m[i]) + (1.0 - beta1) * g;
+    const double v = beta2 * double(tr->adam_v[i]) + (1.0 - beta2) * g * g;
+    tr->adam_m[i] = float(m);
+    tr->adam_v[i] = float(v);
+    const float p = float(double(tr->param[i]) - lr * (m * c1) / (sqrt(v * c2) + eps));
+    tr->param[i] = p;
+    tr->grad[i] = 0.0f;
+    write_net_param(&tr->net, i, p);
+  }
+}
+
+__global__ void k_mlp_adam_finish(pivot_mlp_trainer* tr) {
+  tr->step += 1;
+  tr->loss_sum = 0.0;
+  tr->rows = 0.0;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+namespace pivot {
+namespace detail {
+
+int launch_learned(const Args& a, const pivot_mlp* mlp, double fallback, bool backward, void* stream) {
+  const size_t smem = sizeof(LearnedSmem);
+  static thread_local int configured_device = -1;
+  static thread_local int grid_cap = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
+  if (configured_device != dev) {
+    cudaFuncSetAttribute(k_iv_learned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(k_iv_learned<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int b0 = 0, b1 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_iv_learned<false>, kLBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_iv_learned<true>, kLBlock, smem);
+    const int b = (b0 < b1 ? b0 : b1) > 0 ? (b0 < b1 ? b0 : b1) : 1;
+    grid_cap = b * sm_count();
+    configured_device = dev;
+  }
+  const int64_t tiles = (a.n + kLTile - 1) / kLTile;
+  const unsigned grid = unsigned(tiles < grid_cap ? tiles : grid_cap);
+  const double fb = fallback > 0.0 ? fallback : kDefaultFallback;
+  if (backward)
+    k_iv_learned<true><<<grid, kLBlock, smem, static_cast<cudaStream_t>(stream)>>>(a, mlp, fb);
+  else
+    k_iv_learned<false><<<grid, kLBlock, smem, static_cast<cudaStream_t>(stream)>>>(a, mlp, fb);
+  return launch_status();
+}
+
+}  // namespace detail
+}  // namespace pivot
+
+extern "C" {
+
+int64_t pivot_mlp_trainer_bytes(int64_t* net_offset) {
+  if (net_offset) *net_offset = int64_t(offsetof(pivot_mlp_trainer, net));
+  return int64_t(sizeof(pivot_mlp_trainer));
+}
+
+int pivot_iv_guess(int64_t n, const double* F, const double* K, const double* T, const double* P,
+                   const int8_t* flag, const pivot_opts* opts, double* s_out, void* stream) {
+  if (n < 0) return PIVOT_E_SIZE;
+  const bool learned = opts && opts->mode == PIVOT_MODE_LEARNED;
+  if (opts && opts->mode != PIVOT_MODE_FP64 && !learned) return PIVOT_E_OPTS;
+  if (learned && opts->mlp == nullptr) return PIVOT_E_MLP;
+  if (n == 0) return PIVOT_OK;
+  int dev = -1;
+  const Ptr ps[] = {{F, true, true}, {K, true, true}, {T, true, true}, {P, true, true}, {flag, true, false},
+                    {s_out, true, true}, {learned ? opts->mlp : nullptr, learned, true}};
+  int rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!learned) {
+    k_guess_rational<<<grid_for(n), kBlock, 0, st>>>(n, F, K, T, P, flag, s_out);
+    return launch_status();
+  }
+  const size_t smem = ((sizeof(M::Weights) + 15) / 16) * 16 + size_t(kLWarps) * 2 * M::kRows * M::LDA * 2;
+  cudaFuncSetAttribute(k_guess_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const int64_t chunks = (n + 32 * kLWarps - 1) / (32 * kLWarps);
+  const int64_t cap = int64_t(4) * sm_count();
+  k_guess_mlp<<<unsigned(chunks < cap ? chunks : cap), kLBlock, smem, st>>>(n, F, K, T, P, flag, opts->mlp, s_out);
+  return launch_status();
+}
+
+int pivot_mlp_init(pivot_mlp_trainer* trainer, uint64_t seed, void* stream) {
+  int dev = -1;
+  const Ptr ps[] = {{trainer, true, true}};
+  int rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  k_mlp_init<<<34, 256, 0, static_cast<cudaStream_t>(stream)>>>(trainer, seed);
+  return launch_status();
+}
+
+int pivot_mlp_grad(pivot_mlp_trainer* trainer, int64_t n, const double* F, const double* K, const double* T,
+                   const double* P, const int8_t* flag, const double* sigma, void* stream) {
+  if (n < 0) return PIVOT_E_SIZE;
+  if (n == 0) return PIVOT_OK;
+  int dev = -1;
+  const Ptr ps[] = {{trainer, true, true}, {F, true, true}, {K, true, true}, {T, true, true},
+                    {P, true, true},       {flag, true, false}, {sigma, true, true}};
+  int rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  const size_t smem = sizeof(TrainSmem);
+  cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const int64_t chunks = (n + 32 * kLWarps - 1) / (32 * kLWarps);
+  const int64_t cap = sm_count();
+  k_mlp_grad<<<unsigned(chunks < cap ? chunks : cap), kLBlock, smem, static_cast<cudaStream_t>(stream)>>>(
+      trainer, n, F, K, T, P, flag, sigma);
+  return launch_status();
+}
+
+int pivot_mlp_adam(pivot_mlp_trainer* trainer, double lr, double beta1, double beta2, double eps, void* stream) {
+  if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+    return PIVOT_E_MLP;
+  int dev = -1;
+  const Ptr ps[] = {{trainer, true, true}};
+  int rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_mlp_adam<<<34, 256, 0, st>>>(trainer, lr, beta1, beta2, eps);
+  k_mlp_adam_finish<<<1, 1, 0, st>>>(trainer);
+  return launch_status();
+}
+
+}  // extern "C"

@@ -134,3 +134,41 @@ def per_quote_round_trip(batch, steps: int = 20, lr: float = 1e-2, gated: bool =
         finite_frac.append(float(torch.isfinite(theta).float().mean()))
         losses.append(float(loss.detach()))
     return {"finite_frac": finite_frac, "loss": losses}
+
+
+def operator_pairs(n: int, seed: int = 4, device=None):
+    """Training pairs generated by the operator itself: quotes of the body distribution priced by
+    ``black_price`` and inverted by ``iv`` (the sigma the library returns is the target)."""
+    from . import workloads
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    b = workloads.body_batch(n, seed=seed)
+    t = lambda a: torch.from_numpy(a).to(device)  # noqa: E731
+    F, K, T, flag = t(b.F), t(b.K), t(b.T), t(b.flag)
+    P, _ = api.black_price(F, K, T, t(b.sigma_star), flag, vega=False)
+    sig, _ = api.iv(F, K, T, P, flag, status=False)
+    return F, K, T, P, flag, sig
+
+
+def train_learned_guess(n_rows: int = 16 * 1024 * 1024, steps: int = 4000, batch: int = 65536, lr: float = 3e-3,
+                        seed: int = 4, device=None, log_every: int = 250):
+    """Train the MLP seed of PIVOT_MODE_LEARNED with the library's kernels (pivot_mlp_grad,
+    pivot_mlp_adam) on ``n_rows`` operator-generated pairs; cosine-decayed Adam on random
+    mini-batches.  Returns (trainer, history of (step, mean squared error), seconds)."""
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    F, K, T, P, flag, sig = operator_pairs(n_rows, seed=seed, device=device)
+    trainer = api.MlpTrainer(device, seed=seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    history = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for step in range(steps):
+        idx = torch.randint(0, F.numel(), (batch,), device=device, generator=gen)
+        trainer.grad(F[idx], K[idx], T[idx], P[idx], flag[idx], sig[idx])
+        if step % log_every == 0 or step == steps - 1:
+            _, _, loss_sum, rows, _ = trainer.fields()
+            history.append((step, loss_sum / max(rows, 1.0)))
+        lr_t = 0.5 * lr * (1.0 + math.cos(math.pi * step / steps))
+        trainer.adam(lr_t)
+    torch.cuda.synchronize()
+    return trainer, history, time.perf_counter() - t0
