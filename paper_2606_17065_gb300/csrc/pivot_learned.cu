@@ -29,7 +29,7 @@ struct LearnedSmem {
   double x[kLTile], bmax[kLTile], bb[kLTile], lnb[kLTile], s0[kLTile];
   uint16_t list[kLTile], order[kLTile], pos[kLTile];
   uint8_t bin[kLTile];
-  int nsolve, cnt[2], off[3];
+  int nsolve, cnt[3], off[4];
 };
 
 // The quote's normalised problem and its MLP features (lane = row); `has`
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kLBlock, 2) k_iv_learned(Args a, const pivot_m
   for (int64_t base = int64_t(blockIdx.x) * kLTile; base < a.n; base += int64_t(gridDim.x) * kLTile) {
     if (tid == 0) {
       S.nsolve = 0;
-      S.cnt[0] = S.cnt[1] = 0;
+      S.cnt[0] = S.cnt[1] = S.cnt[2] = 0;
     }
     __syncthreads();
     // ---- phase 1: finish rows that need no solve, list the others
@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(kLBlock, 2) k_iv_learned(Args a, const pivot_m
       if (solve) S.list[slot] = uint16_t(r);
     }
     __syncthreads();
-    // ---- phase 2: MLP seed for the listed rows, 32 per warp; side of the inflection
+    // ---- phase 2: MLP seed for the listed rows, 32 per warp; the row's LBR objective:
+    //      lower below the inflection b_c, middle above it while beta <= b_max/2, upper beyond
     const int nsolve = S.nsolve;
     for (int c = warp; c * 32 < nsolve; c += kLWarps) {
       const int qi = c * 32 + lane;
@@ -105,16 +106,16 @@ __global__ void __launch_bounds__(kLBlock, 2) k_iv_learned(Args a, const pivot_m
       if (has) {
         const double e = pivot::erfcx_fp64(sqrt(-row.x));
         const bool low = row.beta <= 0.5 * row.bmax * (1.0 - e);
-        bin = low ? 0 : 1;
+        bin = low ? 0 : (row.beta <= row.betac ? 1 : 2);
         S.x[r] = row.x;
         S.bmax[r] = row.bmax;
-        S.bb[r] = low ? row.beta : row.betac;
+        S.bb[r] = (bin == 2) ? row.betac : row.beta;
         S.lnb[r] = row.lnb;
         S.s0[r] = row.f.sa * exp(double(o));
         S.bin[r] = uint8_t(bin);
       }
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
+      for (int k = 0; k < 3; ++k) {
         const int p = warp_append(bin == k, &S.cnt[k], lane);
         if (bin == k) S.pos[r] = uint16_t(p);
       }
@@ -123,7 +124,8 @@ __global__ void __launch_bounds__(kLBlock, 2) k_iv_learned(Args a, const pivot_m
     if (tid == 0) {
       S.off[0] = 0;
       S.off[1] = S.cnt[0];
-      S.off[2] = S.cnt[0] + S.cnt[1];
+      S.off[2] = S.off[1] + S.cnt[1];
+      S.off[3] = S.off[2] + S.cnt[2];
     }
     __syncthreads();
     for (int qi = tid; qi < nsolve; qi += kLBlock) {
@@ -131,18 +133,19 @@ __global__ void __launch_bounds__(kLBlock, 2) k_iv_learned(Args a, const pivot_m
       S.order[S.off[S.bin[r]] + S.pos[r]] = uint16_t(r);
     }
     __syncthreads();
-    // ---- phase 3: FP64 Householder steps from the seed, side after side
-    const int total = S.off[2];
+    // ---- phase 3: FP64 Householder steps from the seed, objective after objective
+    const int total = S.off[3];
     for (int qi = tid; qi < total; qi += kLBlock) {
       const int r = S.order[qi];
-      const bool up = qi >= S.off[1];
-      const int rg = up ? pivot::kUpper : pivot::kLower;
+      const int bn = (qi >= S.off[2]) ? 2 : (qi >= S.off[1]) ? 1 : 0;
+      const bool up = bn == 2;
+      const int rg = bn == 0 ? pivot::kLower : bn == 1 ? pivot::kMidHigh : pivot::kUpper;
       const int64_t i = base + r;
       const double F = a.F[i], K = a.K[i], T = a.T[i];
       const int fl = a.flag[i];
       const double x = S.x[r], bb = S.bb[r];
       const double lnbetac = up ? log(bb) : 0.0;
-      const double inv_lnbeta = up ? 0.0 : 1.0 / S.lnb[r];
+      const double inv_lnbeta = (bn == 0) ? 1.0 / S.lnb[r] : 0.0;
       double s = S.s0[r];
       bool ok = s > 0.0 && s < INFINITY;
       if (ok) {
