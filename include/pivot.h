@@ -46,6 +46,7 @@ extern "C" {
 #define PIVOT_E_NOT_DEVICE 5  /* a pointer is not accessible from the current device */
 #define PIVOT_E_ALIGN 6       /* a float64 pointer is not 8-byte aligned */
 #define PIVOT_E_MLP 7         /* PIVOT_MODE_LEARNED without weights, or bad training hyper-parameters */
+#define PIVOT_E_TOO_MANY 8    /* n above the row limit of pivot_mlp_grad_static */
 
 /* ---- per-row status codes (uint8) --------------------------------------- */
 #define PIVOT_ROW_OK 0              /* sigma finite and > 0 */
@@ -208,6 +209,32 @@ int pivot_mlp_grad(pivot_mlp_trainer* trainer, int64_t n, const double* F, const
                    void* stream);
 int pivot_mlp_adam(pivot_mlp_trainer* trainer, double lr, double beta1, double beta2, double eps,
                    void* stream);
+
+/*
+ * pivot_mlp_grad_static -- the gradient pass of pivot_mlp_grad without any
+ * device allocation, for callers that cannot allocate device memory: code
+ * that runs inside a host framework which owns every device buffer (a
+ * cudaMalloc there would bypass its allocator and its memory budget), or
+ * that works on a device whose memory is already fully handed out.  The paper
+ * has no counterpart; it exists for deployment.
+ *   in : net (the BF16 weights, e.g. &trainer->net), n rows of F, K, T, P
+ *        (float64), flag (int8), sigma (float64) as for pivot_mlp_grad
+ *   out: grad_out (PIVOT_MLP_NPARAM float32, the gradient of the sum of
+ *        squared errors over the rows, in the flat parameter order),
+ *        loss_out (2 float64: that sum, and the number of rows in it)
+ * Scratch: the FP32 accumulator (PIVOT_MLP_NPARAM floats) and the two sums
+ * live in one static device array of the library (34,328 bytes per device
+ * that loads the library, held until the process exits).  Each call clears
+ * it first and copies the result out; calls that overlap on the GPU (two
+ * streams, two host threads) share the array and race.  n is limited to
+ * 2^26 rows per call (FP32 sums over more rows lose their last digits):
+ * larger n returns PIVOT_E_TOO_MANY and launches nothing.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.
+ */
+int pivot_mlp_grad_static(const pivot_mlp* net, int64_t n, const double* F, const double* K,
+                          const double* T, const double* P, const int8_t* flag, const double* sigma,
+                          float* grad_out, double* loss_out, void* stream);
 
 /* sizeof(pivot_mlp_trainer) and offsetof(pivot_mlp_trainer, net), for bindings. */
 int64_t pivot_mlp_trainer_bytes(int64_t* net_offset);

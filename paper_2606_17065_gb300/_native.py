@@ -36,6 +36,7 @@ _SIGNATURES = {
     "pivot_mlp_init": [c_vp, ctypes.c_uint64, c_vp],
     "pivot_mlp_grad": [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
     "pivot_mlp_adam": [c_vp, c_dbl, c_dbl, c_dbl, c_dbl, c_vp],
+    "pivot_mlp_grad_static": [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
     "pivot_error_string": [ctypes.c_int],
     "pivot_version": [],
 }

@@ -443,6 +443,7 @@ const char* pivot_error_string(int code) {
     case PIVOT_E_NOT_DEVICE: return "a pointer is not device memory of the current device";
     case PIVOT_E_ALIGN: return "a float64 pointer is not 8-byte aligned";
     case PIVOT_E_MLP: return "learned mode without weights, or bad training hyper-parameters";
+    case PIVOT_E_TOO_MANY: return "n above the row limit of pivot_mlp_grad_static (2^26)";
     default: break;
   }
   if (code < 0) return cudaGetErrorString(static_cast<cudaError_t>(-code));

@@ -471,3 +471,126 @@ int pivot_mlp_adam(pivot_mlp_trainer* trainer, double lr, double beta1, double b
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// pivot_mlp_grad_static: the gradient pass of pivot_mlp_grad for callers that
+// cannot allocate device memory.  Its scratch (the FP32 gradient accumulator
+// and the two loss sums) is a fixed array inside the library instead of the
+// caller's pivot_mlp_trainer; the result is copied to the caller's outputs.
+// ---------------------------------------------------------------------------
+namespace {
+
+// rows one call may cover: FP32 sums over more rows lose their last digits
+constexpr int64_t kStaticGradMaxRows = int64_t(1) << 26;
+// PIVOT_MLP_NPARAM accumulators, padded to an 8-byte boundary, then 2 doubles
+constexpr int kStaticLossOffset = ((PIVOT_MLP_NPARAM + 1) / 2) * 2;
+constexpr int kStaticScratchFloats = kStaticLossOffset + 4;
+
+static __device__ __align__(256) float g_mlp_grad_scratch[kStaticScratchFloats];
+
+__global__ void k_static_scratch_zero(float* scratch) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kStaticScratchFloats; i += gridDim.x * blockDim.x)
+    scratch[i] = 0.0f;
+}
+
+__global__ void __launch_bounds__(kLBlock, 1)
+    k_mlp_grad_static(const pivot_mlp* net, int64_t n, const double* __restrict__ F, const double* __restrict__ K,
+                      const double* __restrict__ T, const double* __restrict__ P, const int8_t* __restrict__ flag,
+                      const double* __restrict__ sigma, float* scratch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  M::stage_weights(net, S.W, &S.WT);
+  __syncthreads();
+  float sq = 0.0f;
+  int nvalid = 0;
+  for (int64_t c0 = (int64_t(blockIdx.x) * kLWarps + warp) * 32; c0 < n; c0 += int64_t(gridDim.x) * kLWarps * 32) {
+    const int64_t i = c0 + lane;
+    bool valid = false;
+    float f0 = 0.0f, f1 = 0.5f, y = 0.0f;
+    if (i < n) {
+      const double sg = sigma[i];
+      const pivot::Quote q = pivot::classify_quote(F[i], K[i], T[i], P[i], flag[i]);
+      if (q.status == 0 && sg > 0.0 && sg < INFINITY) {
+        const LearnedRow row = learned_row(F[i], K[i], T[i], P[i], flag[i]);
+        const double target = log(sg * sqrt(T[i]) / row.f.sa);
+        if (row.f.sa > 0.0 && fabs(target) < 1e30) {
+          valid = true;
+          f0 = row.f.f0;
+          f1 = row.f.f1;
+          y = float(target);
+        }
+      }
+    }
+    sq += M::train_warp(f0, f1, y, valid, S.W, S.WT, S.tiles[warp], scratch);
+    nvalid += valid ? 1 : 0;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    nvalid += __shfl_xor_sync(0xffffffffu, nvalid, off);
+  }
+  if (lane == 0) {
+    double* loss = reinterpret_cast<double*>(scratch + kStaticLossOffset);
+    atomicAdd(loss, double(sq));
+    atomicAdd(loss + 1, double(nvalid));
+  }
+}
+
+__global__ void k_static_scratch_copy_out(const float* scratch, float* grad_out, double* loss_out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < PIVOT_MLP_NPARAM; i += gridDim.x * blockDim.x)
+    grad_out[i] = scratch[i];
+  if (blockIdx.x == 0 && threadIdx.x < 2)
+    loss_out[threadIdx.x] = reinterpret_cast<const double*>(scratch + kStaticLossOffset)[threadIdx.x];
+}
+
+// device address of the static scratch, looked up once per device with that device current
+int static_scratch(float** out) {
+  constexpr int kMaxDevices = 64;
+  static float* addr[kMaxDevices] = {};
+  int dev = 0;
+  const cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 != cudaSuccess) return -int(e0);
+  if (dev < 0 || dev >= kMaxDevices) return PIVOT_E_NOT_DEVICE;
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_mlp_grad_scratch);
+    if (e != cudaSuccess) return -int(e);
+    addr[dev] = static_cast<float*>(p);
+  }
+  *out = addr[dev];
+  return PIVOT_OK;
+}
+
+}  // namespace
+
+extern "C" int pivot_mlp_grad_static(const pivot_mlp* net, int64_t n, const double* F, const double* K,
+                                     const double* T, const double* P, const int8_t* flag, const double* sigma,
+                                     float* grad_out, double* loss_out, void* stream) {
+  if (n < 0) return PIVOT_E_SIZE;
+  if (n > kStaticGradMaxRows) return PIVOT_E_TOO_MANY;
+  if (reinterpret_cast<uintptr_t>(net) & 3u || reinterpret_cast<uintptr_t>(grad_out) & 3u) return PIVOT_E_ALIGN;
+  int dev = -1;
+  const Ptr ps[] = {{net, true, false},     {grad_out, true, false}, {loss_out, true, true},
+                    {F, n > 0, true},       {K, n > 0, true},        {T, n > 0, true},
+                    {P, n > 0, true},       {flag, n > 0, false},    {sigma, n > 0, true}};
+  int rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  float* scratch = nullptr;
+  rc = static_scratch(&scratch);
+  if (rc != PIVOT_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's sums: clear it first
+  k_static_scratch_zero<<<34, 256, 0, st>>>(scratch);
+  if (n > 0) {
+    const size_t smem = sizeof(TrainSmem);
+    cudaFuncSetAttribute(k_mlp_grad_static, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const int64_t chunks = (n + 32 * kLWarps - 1) / (32 * kLWarps);
+    const int64_t cap = sm_count();
+    k_mlp_grad_static<<<unsigned(chunks < cap ? chunks : cap), kLBlock, smem, st>>>(net, n, F, K, T, P, flag, sigma,
+                                                                                    scratch);
+  }
+  k_static_scratch_copy_out<<<34, 256, 0, st>>>(scratch, grad_out, loss_out);
+  return launch_status();
+}
