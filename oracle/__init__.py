@@ -48,8 +48,11 @@ def _bind(lib):
     lib.oracle_iv.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.oracle_iv_grad.argtypes = [i64, vp, vp, vp, vp, vp, vp, d, i32, vp, vp, vp, vp, i32]
     lib.oracle_black_price_grad.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    lib.oracle_bs_price.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    lib.oracle_bs_iv.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    lib.oracle_bs_iv_grad.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, d, i32, vp, vp, vp, vp, vp, vp, i32]
     for name in ("oracle_black_price", "oracle_iv", "oracle_iv_grad", "oracle_black_price_grad",
-                 "oracle_max_threads"):
+                 "oracle_bs_price", "oracle_bs_iv", "oracle_bs_iv_grad", "oracle_max_threads"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -161,6 +164,59 @@ class Oracle:
         if rc:
             raise ValueError(f"oracle_iv_grad returned {rc}")
         return tuple(out)
+
+    # -- Black-Scholes interface on xi = (S, K, tau, r, q) -------------------------------------
+    def bs_price(self, S, K, T, r, q, sigma, flag, nthreads: int = 1):
+        """Discounted Black-Scholes price and cash vega, Eq. app_black_scholes."""
+        S, K, T, r, q, sigma = map(_f64, (S, K, T, r, q, sigma))
+        flag = np.ascontiguousarray(flag, dtype=np.int8)
+        n = S.shape[0]
+        V = np.empty(n)
+        vega = np.empty(n)
+        rc = self.lib.oracle_bs_price(n, _ptr(S), _ptr(K), _ptr(T), _ptr(r), _ptr(q), _ptr(sigma), _ptr(flag),
+                                      _ptr(V), _ptr(vega), nthreads)
+        if rc:
+            raise ValueError(f"oracle_bs_price returned {rc}")
+        return V, vega
+
+    def bs_implied_vol(self, S, K, T, r, q, V, flag, nthreads: int = 1):
+        """sigma and status per row from the discounted price (Algorithm 1 forward normalisation)."""
+        S, K, T, r, q, V = map(_f64, (S, K, T, r, q, V))
+        flag = np.ascontiguousarray(flag, dtype=np.int8)
+        n = S.shape[0]
+        sig = np.empty(n)
+        st = np.empty(n, dtype=np.uint8)
+        rc = self.lib.oracle_bs_iv(n, _ptr(S), _ptr(K), _ptr(T), _ptr(r), _ptr(q), _ptr(V), _ptr(flag), _ptr(sig),
+                                   _ptr(st), nthreads)
+        if rc:
+            raise ValueError(f"oracle_bs_iv returned {rc}")
+        return sig, st
+
+    def bs_iv_grad(self, S, K, T, r, q, flag, sigma, gbar=None, tau: float = 0.0, gate_mode: int = 0,
+                   nthreads: int = 1):
+        """(dV, dS, dK, dT, dr, dq): Algorithm 1 backward on xi with the gate of Section 3.3."""
+        S, K, T, r, q, sigma = map(_f64, (S, K, T, r, q, sigma))
+        flag = np.ascontiguousarray(flag, dtype=np.int8)
+        g = None if gbar is None else _f64(gbar)
+        n = S.shape[0]
+        out = [np.empty(n) for _ in range(6)]
+        rc = self.lib.oracle_bs_iv_grad(n, _ptr(S), _ptr(K), _ptr(T), _ptr(r), _ptr(q), _ptr(flag), _ptr(sigma),
+                                        _ptr(g), float(tau), int(gate_mode), *[_ptr(o) for o in out], nthreads)
+        if rc:
+            raise ValueError(f"oracle_bs_iv_grad returned {rc}")
+        return tuple(out)
+
+
+def bs_price(*a, **k):
+    return default().bs_price(*a, **k)
+
+
+def bs_implied_vol(*a, **k):
+    return default().bs_implied_vol(*a, **k)
+
+
+def bs_iv_grad(*a, **k):
+    return default().bs_iv_grad(*a, **k)
 
 
 def black_price_grad(*a, **k):

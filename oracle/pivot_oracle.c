@@ -610,3 +610,157 @@ int oracle_black_price_grad(int64_t n, const double* F, const double* K, const d
   (void)nthreads;
   return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * The Black-Scholes interface on xi = (S, K, tau, r, q) (Section 2, Eq.
+ * app_forward_price and Eq. app_black_scholes; Section 3, Algorithm 1).
+ *
+ *  - Price: Eq. app_black_scholes equals the discounted Black-76 price in
+ *    forward coordinates (Eq. app_black76): V = e^{-r tau} B(F, K, tau, sigma)
+ *    with F = S e^{(r - q) tau}.
+ *  - Implied volatility: Algorithm 1's forward normalisation, F = S e^{(r-q) tau}
+ *    and B = e^{r tau} V, then the Black-76 inversion above.  Rows with a
+ *    non-finite r or q are bad inputs (status 3).
+ *  - Adjoint: Algorithm 1's backward, Vbar = gbar / V_bs and
+ *    xibar = -gbar (dV/dxi) / V_bs, with the Greeks of Eq. app_black_scholes
+ *    differentiated directly (theta = +1 call, -1 put, M = Phi/phi):
+ *      V_bs     = S e^{-q tau} phi(d1) sqrt(tau)            (vega)
+ *      dV/dS    =  theta e^{-q tau} Phi(theta d1)
+ *      dV/dK    = -theta e^{-r tau} Phi(theta d2)
+ *      dV/dr    =  theta K tau e^{-r tau} Phi(theta d2)
+ *      dV/dq    = -theta S tau e^{-q tau} Phi(theta d1)
+ *      dV/dtau  =  V_bs sigma/(2 tau) - theta q S e^{-q tau} Phi(theta d1)
+ *                 + theta r K e^{-r tau} Phi(theta d2)
+ *    and, with S e^{-q tau} phi(d1) = K e^{-r tau} phi(d2), each ratio to V_bs
+ *    is a Mills ratio times a plain factor.  The gate of Section 3.3 compares
+ *    V_bs (the derivative of the cash price in sigma) with tau_gate.
+ * ------------------------------------------------------------------------- */
+static int bs_to_black(double S, double T, double r, double q, double Vm, double* F, double* B) {
+  if (!isfinite(r) || !isfinite(q)) return 1;
+  *F = S * exp((r - q) * T);
+  *B = Vm * exp(r * T);
+  return 0;
+}
+
+int oracle_bs_price(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                    const double* q, const double* sigma, const int8_t* flag, double* V, double* vega,
+                    int nthreads) {
+  if (n < 0) return 1;
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    double F, unused, P, Vb;
+    if (bs_to_black(S[i], T[i], r[i], q[i], 0.0, &F, &unused)) {
+      V[i] = NAN;
+      if (vega) vega[i] = NAN;
+      continue;
+    }
+    black_row(F, K[i], T[i], sigma[i], flag[i], &P, &Vb);
+    double disc = exp(-r[i] * T[i]);
+    V[i] = disc * P;
+    if (vega) vega[i] = disc * Vb;
+  }
+  (void)nthreads;
+  return 0;
+}
+
+int oracle_bs_iv(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                 const double* q, const double* Vm, const int8_t* flag, double* sigma, uint8_t* status,
+                 int nthreads) {
+  if (n < 0) return 1;
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    uint8_t st;
+    double F, B;
+    if (bs_to_black(S[i], T[i], r[i], q[i], Vm[i], &F, &B)) {
+      sigma[i] = NAN;
+      st = 3;
+    } else {
+      iv_row(F, K[i], T[i], B, flag[i], &sigma[i], &st);
+    }
+    if (status) status[i] = st;
+  }
+  (void)nthreads;
+  return 0;
+}
+
+static void bs_grad_row(double S, double K, double T, double r, double q, int8_t flag, double sig, double g,
+                        double tau, int mode, double out[6]) {
+  int k;
+  if (bad_inputs(S, K, T, flag) || !isfinite(r) || !isfinite(q) || isnan(sig) || sig < 0.0 || isnan(g)) {
+    for (k = 0; k < 6; ++k) out[k] = NAN;
+    return;
+  }
+  if (sig == 0.0 || isinf(sig)) {
+    double v = NAN;
+    if (mode == 1) v = (g == 0.0) ? 0.0 : NAN;
+    if (mode == 2 || mode == 3) v = 0.0;
+    for (k = 0; k < 6; ++k) out[k] = v;
+    return;
+  }
+  int theta = flag;
+  double sqT = sqrt(T);
+  double s = sig * sqT;
+  double x = log(S / K) + (r - q) * T; /* ln(F/K), Eq. app_black_scholes's d1 numerator */
+  double d1 = x / s + 0.5 * s, d2 = d1 - s;
+  double Vbs = exp(log(S) - q * T - 0.5 * d1 * d1 - LN_SQRT_2PI) * sqT;
+  double M1 = oracle_mills(theta * d1), M2 = oracle_mills(theta * d2);
+  double j[6];
+  j[0] = 1.0 / Vbs;                                             /* dsigma/dV   */
+  j[1] = -theta * M1 / (S * sqT);                               /* dsigma/dS   */
+  j[2] = theta * M2 / (K * sqT);                                /* dsigma/dK   */
+  j[3] = -sig / (2.0 * T) + theta * (q * M1 - r * M2) / sqT;    /* dsigma/dtau */
+  j[4] = -theta * sqT * M2;                                     /* dsigma/dr   */
+  j[5] = theta * sqT * M1;                                      /* dsigma/dq   */
+  int in_g = fabs(Vbs) > tau;
+  if (mode == 0 || ((mode == 1 || mode == 2) && in_g)) {
+    for (k = 0; k < 6; ++k) out[k] = g * j[k];
+    return;
+  }
+  if (mode == 1 || mode == 2) {
+    double v = (mode == 1 && g != 0.0) ? NAN : 0.0;
+    for (k = 0; k < 6; ++k) out[k] = v;
+    return;
+  }
+  double w, wP;
+  if (Vbs > tau) {
+    double rr = tau / Vbs;
+    w = 1.0 / (1.0 + rr * rr);
+    wP = w / Vbs;
+  } else {
+    double rr = Vbs / tau;
+    w = rr * rr / (1.0 + rr * rr);
+    wP = (rr / tau) / (1.0 + rr * rr);
+  }
+  out[0] = g * wP;
+  for (k = 1; k < 6; ++k) out[k] = g * j[k] * w;
+}
+
+int oracle_bs_iv_grad(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                      const double* q, const int8_t* flag, const double* sigma, const double* gbar,
+                      double tau, int gate_mode, double* dV, double* dS, double* dK, double* dT,
+                      double* dr, double* dq, int nthreads) {
+  if (n < 0 || gate_mode < 0 || gate_mode > 3 || !(tau >= 0.0)) return 1;
+  if (gate_mode == 3 && !(tau > 0.0)) return 1;
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    double o[6];
+    bs_grad_row(S[i], K[i], T[i], r[i], q[i], flag[i], sigma[i], gbar ? gbar[i] : 1.0, tau, gate_mode, o);
+    if (dV) dV[i] = o[0];
+    if (dS) dS[i] = o[1];
+    if (dK) dK[i] = o[2];
+    if (dT) dT[i] = o[3];
+    if (dr) dr[i] = o[4];
+    if (dq) dq[i] = o[5];
+  }
+  (void)nthreads;
+  return 0;
+}

@@ -48,6 +48,19 @@ int oracle_iv_grad(int64_t n, const double* F, const double* K, const double* T,
 int oracle_black_price_grad(int64_t n, const double* F, const double* K, const double* T,
                             const double* sigma, const int8_t* flag, const double* gbar,
                             double* dsigma, double* dF, double* dK, double* dT, int nthreads);
+/* Black-Scholes interface on xi = (S, K, T = tau, r, q), V the discounted price:
+ * price and vega dV/dsigma; sigma and status; the gated VJP
+ * (dV, dS, dK, dT, dr, dq), the gate comparing the cash vega with tau. */
+int oracle_bs_price(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                    const double* q, const double* sigma, const int8_t* flag, double* V, double* vega,
+                    int nthreads);
+int oracle_bs_iv(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                 const double* q, const double* Vm, const int8_t* flag, double* sigma, uint8_t* status,
+                 int nthreads);
+int oracle_bs_iv_grad(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                      const double* q, const int8_t* flag, const double* sigma, const double* gbar,
+                      double tau, int gate_mode, double* dV, double* dS, double* dK, double* dT,
+                      double* dr, double* dq, int nthreads);
 /* number of threads OpenMP would use for nthreads <= 0 */
 int oracle_max_threads(void);
 

@@ -175,3 +175,44 @@ def low_vega_chain(n: int = 65536, seed: int = 31) -> Batch:
     sig = rng.uniform(0.05, 1.0, n)
     flag = np.where(k > 0, 1, -1).astype(np.int8)
     return Batch(F, F * np.exp(k), T, sig, flag)
+
+
+@dataclass
+class BSBatch:
+    """Rows of the Black-Scholes interface: xi = (S, K, tau, r, q) and the flag (Section 2)."""
+    S: np.ndarray
+    K: np.ndarray
+    T: np.ndarray
+    r: np.ndarray
+    q: np.ndarray
+    sigma_star: np.ndarray
+    flag: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.S.shape[0])
+
+    def subset(self, idx) -> "BSBatch":
+        return BSBatch(*(getattr(self, f)[idx] for f in ("S", "K", "T", "r", "q", "sigma_star", "flag")))
+
+
+def bs_batch(n: int = SMALL_N, seed: int = 6, wide: bool = False) -> BSBatch:
+    """S = 100, ln(K/S) ~ U[-1,1] (U[-6,6] with ``wide``), T ~ U[1/365, 3], sigma* ~ U[0.05, 1]
+    (s = sigma sqrt(T) log-uniform on [1e-4, 3] with ``wide``), r ~ U[-0.01, 0.08],
+    q ~ U[0, 0.05], calls/puts 50/50.
+
+    The spot-coordinate form of the canonical grid: rates and dividend yields of listed
+    equity-index options, negative rates included (Section 2, the tuple xi).  The
+    discounted prices V come from a Black-Scholes price evaluated by the caller.
+    """
+    rng = np.random.default_rng(seed)
+    S = np.full(n, 100.0)
+    K = S * np.exp(rng.uniform(-6.0, 6.0, n) if wide else rng.uniform(-1.0, 1.0, n))
+    T = rng.uniform(1.0 / 365.0, 3.0, n)
+    if wide:
+        sig = 10.0 ** rng.uniform(-4.0, np.log10(3.0), n) / np.sqrt(T)
+    else:
+        sig = rng.uniform(0.05, 1.0, n)
+    r = rng.uniform(-0.01, 0.08, n)
+    q = rng.uniform(0.0, 0.05, n)
+    return BSBatch(S, K, T, r, q, sig, _flags(rng, n))

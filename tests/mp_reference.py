@@ -84,3 +84,48 @@ def iv_gradient_fd(F, K, T, P, theta, rel_h=mp.mpf("1e-15")):
         s_dn = implied_vol(*dn, theta)
         out.append((s_up - s_dn) / (2 * h))
     return out  # d sigma / d(P, F, K, T)
+
+
+def bs_price(S, K, T, r, q, sigma, theta):
+    """Discounted Black-Scholes price, Eq. app_black_scholes in spot coordinates (put by the
+    direct put formula, not parity)."""
+    S, K, T, r, q, sigma = map(mp.mpf, (S, K, T, r, q, sigma))
+    s = sigma * mp.sqrt(T)
+    d1 = (mp.log(S / K) + (r - q) * T + s * s / 2) / s
+    d2 = d1 - s
+    if theta > 0:
+        return S * mp.e ** (-q * T) * mp.ncdf(d1) - K * mp.e ** (-r * T) * mp.ncdf(d2)
+    return K * mp.e ** (-r * T) * mp.ncdf(-d2) - S * mp.e ** (-q * T) * mp.ncdf(-d1)
+
+
+def bs_implied_vol(S, K, T, r, q, V, theta, iters: int = 200):
+    """Root of bs_price(sigma) = V by bisection in ln(sigma); None outside the price interval."""
+    S, K, T, r, q, V = map(mp.mpf, (S, K, T, r, q, V))
+    lo_p = bs_price(S, K, T, r, q, mp.mpf("1e-30"), theta)
+    hi_p = bs_price(S, K, T, r, q, mp.mpf("1e6"), theta)
+    if not (lo_p < V < hi_p):
+        return None
+    lo, hi = mp.log(mp.mpf("1e-12")), mp.log(mp.mpf("1e4"))
+    for _ in range(iters):
+        mid = (lo + hi) / 2
+        if bs_price(S, K, T, r, q, mp.e ** mid, theta) < V:
+            lo = mid
+        else:
+            hi = mid
+    return mp.e ** ((lo + hi) / 2)
+
+
+def bs_iv_gradient_fd(S, K, T, r, q, V, theta, h=mp.mpf("1e-20")):
+    """Central differences of the high-precision root in (V, S, K, T, r, q); steps are
+    relative for V, S, K, T and absolute for r, q."""
+    base = [mp.mpf(a) for a in (V, S, K, T, r, q)]
+    out = []
+    for j in range(6):
+        step = h * (base[j] if j < 4 else 1)
+        up, dn = list(base), list(base)
+        up[j] += step
+        dn[j] -= step
+        s_up = bs_implied_vol(up[1], up[2], up[3], up[4], up[5], up[0], theta)
+        s_dn = bs_implied_vol(dn[1], dn[2], dn[3], dn[4], dn[5], dn[0], theta)
+        out.append((s_up - s_dn) / (2 * step))
+    return out  # d sigma / d(V, S, K, T, r, q)
