@@ -286,6 +286,88 @@ def body_variants(dev, stream, steps):
             "rows": n, "plain_fp64": plain, "mixed": mixed, "learned": learned,
             "mixed_speedup": plain["ms_per_step"] / mixed["ms_per_step"],
             "learned_speedup": plain["ms_per_step"] / learned["ms_per_step"]}
+def bs_variants(dev, stream, steps):
+    """The Black-Scholes interface on xi = (S, K, tau, r, q): fused fwd+bwd on a 16M-row batch
+    of the wide distribution (ln(K/S) ~ U[-6,6], s log-uniform on [1e-4, 3], r ~ U[-0.01, 0.08],
+    q ~ U[0, 0.05]), and the streaming label loop: 64 batches of 65,536 quotes copied from
+    pinned host memory, inverted (forward only) and copied back, on two alternating streams."""
+    import ctypes
+
+    import torch
+
+    import paper_2606_17065_gb300 as pv
+    from paper_2606_17065_gb300 import _native
+    b = workloads.bs_batch(workloads.STRESS_N, seed=7, wide=True)
+    n = b.n
+    S, K, T, r, q, s0 = (torch.from_numpy(a).to(dev) for a in (b.S, b.K, b.T, b.r, b.q, b.sigma_star))
+    flag = torch.from_numpy(b.flag).to(dev)
+    V, _ = pv.bs_price(S, K, T, r, q, s0, flag, vega=False)
+    sig = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+    g = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(6)]
+    lib = _native.lib()
+    p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    opts = _native.PivotOpts()
+
+    def run(mode, backward=True, strm=stream, m=n, ins=None, out=None):
+        opts.mode, opts.householder = mode, 0
+        a = ins or (S, K, T, r, q, V, flag)
+        if backward:
+            rc = lib.pivot_bs_iv_forward_backward(m, *[p(x) for x in a], None, TAU, pv.GATES[GATE], p(sig), p(st),
+                                                  *[p(x) for x in g], ctypes.byref(opts),
+                                                  ctypes.c_void_p(strm.cuda_stream))
+        else:
+            rc = lib.pivot_bs_iv_forward(m, *[p(x) for x in a], p(out if out is not None else sig), None,
+                                         ctypes.byref(opts), ctypes.c_void_p(strm.cuda_stream))
+        if rc != 0:
+            raise RuntimeError(_native.error_string(rc))
+
+    plain = time_variant(lambda: run(0), n, stream, steps)
+    mixed = time_variant(lambda: run(1), n, stream, steps)
+    fwd = time_variant(lambda: run(0, backward=False), n, stream, steps)
+
+    # streaming label generation from host memory
+    nb, m = 64, 65536
+    host = [torch.from_numpy(np.ascontiguousarray(a[:nb * m])).pin_memory()
+            for a in (b.S, b.K, b.T, b.r, b.q)]
+    host.append(V[:nb * m].cpu().pin_memory())
+    host.append(torch.from_numpy(b.flag[:nb * m]).pin_memory())
+    labels = torch.empty(nb * m, dtype=torch.float64).pin_memory()
+    streams = [torch.cuda.Stream(dev) for _ in range(2)]
+    bufs = [[torch.empty(m, dtype=h.dtype, device=dev) for h in host] + [torch.empty(m, dtype=torch.float64,
+                                                                                    device=dev)]
+            for _ in range(2)]
+
+    def pipeline():
+        for j in range(nb):
+            k = j % 2
+            with torch.cuda.stream(streams[k]):
+                for d, h in zip(bufs[k][:7], host):
+                    d.copy_(h[j * m:(j + 1) * m], non_blocking=True)
+                run(0, backward=False, strm=streams[k], m=m, ins=bufs[k][:7], out=bufs[k][7])
+                labels[j * m:(j + 1) * m].copy_(bufs[k][7], non_blocking=True)
+        for s_ in streams:
+            s_.synchronize()
+
+    for _ in range(2):
+        pipeline()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        pipeline()
+    wall = (time.perf_counter() - t0) / reps
+    ok = bool(torch.isfinite(labels[:1024]).any())
+    label_rate = {"value": nb * m / wall, "unit": "labels/s", "ms_per_loop": wall * 1e3, "batches": nb,
+                  "batch_rows": m, "h2d_bytes_per_loop": nb * m * 49, "d2h_bytes_per_loop": nb * m * 8,
+                  "labels_finite": ok}
+    del S, K, T, r, q, s0, flag, V, sig, st, g, bufs
+    torch.cuda.empty_cache()
+    return {"workload": "bs-wide-16M: S=100, ln(K/S)~U[-6,6], sigma*sqrt(T) log-uniform [1e-4,3], T~U[1/365,3], "
+                        "r~U[-0.01,0.08], q~U[0,0.05], fwd+bwd in (V,S,K,tau,r,q)",
+            "rows": n, "plain_fp64": plain, "mixed": mixed, "forward_only": fwd,
+            "label_pipeline": label_rate}
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -406,6 +488,7 @@ def run_ours(args, rank, world):
                    "frac": BYTES_PER_ROW * n / (mean_ms * 1e-3) / 1e9 / hbm_peak}
 
     body = body_variants(dev, stream, max(args.steps // 4, 2)) if args.rows == workloads.STRESS_N else None
+    bsv = bs_variants(dev, stream, max(args.steps // 4, 2)) if args.rows == workloads.STRESS_N else None
 
     cpu = None
     if rank == 0 and world == 1:
@@ -427,7 +510,8 @@ def run_ours(args, rank, world):
                 "forward_only": {"value": n * world / (fwd_ms * 1e-3), "unit": UNIT, "ms_per_step": fwd_ms},
                 "variants": {"mixed_same_workload": mixed,
                              "mixed_speedup_same_workload": ms_per_step / mixed["ms_per_step"],
-                             "body_64M": body},
+                             "body_64M": body,
+                             "black_scholes_16M": bsv},
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
 

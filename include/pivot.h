@@ -179,6 +179,49 @@ int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const
                               double* dT, const pivot_opts* opts, void* stream);
 
 /*
+ * Black-Scholes interface on the paper's tuple xi = (S, K, tau, r, q) (Section 2,
+ * Eq. app_forward_price and Eq. app_black_scholes; Section 3, Algorithm 1).
+ * Row inputs: spot S, strike K, time to expiry T (the paper's tau, years),
+ * risk-free rate r and dividend yield / cost of carry q (continuous, any
+ * finite sign), the DISCOUNTED market price V, flag +1 call / -1 put; all
+ * float64 except the int8 flag, device memory of one device.
+ * Forward (Algorithm 1): F = S e^{(r-q) T}, B = e^{r T} V, then the Black-76
+ * inversion of pivot_iv_forward on (F, K, T, B); the status codes refer to B
+ * against the Black-76 bounds, i.e. V against the discounted intrinsic value
+ * e^{-r T} max(theta (F - K), 0) and the discounted upper bound (S e^{-q T}
+ * for calls, K e^{-r T} for puts).  A non-finite r or q is a bad input.
+ * Backward (Algorithm 1, Eq. method_vjp): dV = gbar / V_bs and
+ * d(S, K, T, r, q) = -gbar (dV/d(S, K, T, r, q)) / V_bs, V_bs = dV/dsigma the
+ * cash vega; the gate of Section 3.3 compares V_bs with tau.
+ * PIVOT_MODE_LEARNED is not offered on this form (PIVOT_E_OPTS): its seed was
+ * trained on Black-76 rows only; FP64 and MIXED are.
+ */
+
+/* V = e^{-r T} B(F, K, T, sigma) and, if vega_out is not NULL, dV/dsigma. */
+int pivot_bs_price(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                   const double* q, const double* sigma, const int8_t* flag, double* V_out,
+                   double* vega_out, void* stream);
+
+/* sigma (required) and status (may be NULL) per row; opts as for pivot_iv_forward. */
+int pivot_bs_iv_forward(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                        const double* q, const double* V, const int8_t* flag, double* sigma_out,
+                        uint8_t* status_out, const pivot_opts* opts, void* stream);
+
+/* The gated VJP from the saved (S, K, T, r, q, flag, sigma); gbar, tau and
+ * gate_mode as for pivot_iv_backward; each output may be NULL. */
+int pivot_bs_iv_backward(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                         const double* q, const int8_t* flag, const double* sigma, const double* gbar,
+                         double tau, int32_t gate_mode, double* dV, double* dS, double* dK, double* dT,
+                         double* dr, double* dq, void* stream);
+
+/* Both in one pass over HBM. */
+int pivot_bs_iv_forward_backward(int64_t n, const double* S, const double* K, const double* T,
+                                 const double* r, const double* q, const double* V, const int8_t* flag,
+                                 const double* gbar, double tau, int32_t gate_mode, double* sigma_out,
+                                 uint8_t* status_out, double* dV, double* dS, double* dK, double* dT,
+                                 double* dr, double* dq, const pivot_opts* opts, void* stream);
+
+/*
  * pivot_mills_ratio -- Y(z) = Phi(z)/phi(z), the ratio through which the
  * adjoint writes Delta/V (Eq. implicit_iv with F phi(d1) = K phi(d2)) and the
  * normalised Black function writes b/b_s (Section 2, Eq. app_normalized_black).

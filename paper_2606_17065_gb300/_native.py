@@ -30,6 +30,10 @@ _SIGNATURES = {
     "pivot_iv_backward": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp],
     "pivot_iv_forward_backward": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_dbl, c_i32, c_vp, c_vp, c_vp, c_vp,
                                   c_vp, c_vp, c_vp, c_vp],
+    "pivot_bs_price": [c_i64] + [c_vp] * 10,
+    "pivot_bs_iv_forward": [c_i64] + [c_vp] * 11,
+    "pivot_bs_iv_backward": [c_i64] + [c_vp] * 8 + [c_dbl, ctypes.c_int32] + [c_vp] * 7,
+    "pivot_bs_iv_forward_backward": [c_i64] + [c_vp] * 8 + [c_dbl, ctypes.c_int32] + [c_vp] * 10,
     "pivot_mills_ratio": [c_i64, c_vp, c_vp, c_vp],
     "pivot_mlp_trainer_bytes": [c_vp],
     "pivot_iv_guess": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],

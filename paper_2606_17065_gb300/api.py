@@ -283,3 +283,95 @@ class BlackPrice(torch.autograd.Function):
 def black_price_autograd(sigma, F, K, T, flag):
     """Differentiable Black-76 price, see ``BlackPrice``."""
     return BlackPrice.apply(sigma, F, K, T, flag)
+
+
+# ---------------------------------------------------------------------------------------------
+# Black-Scholes interface on xi = (S, K, tau, r, q) with the discounted price V (Section 2,
+# Eq. app_black_scholes; Algorithm 1).  T is the paper's tau (years); the gate threshold keeps
+# the name ``tau`` as in the Black-76 calls.
+# ---------------------------------------------------------------------------------------------
+def bs_price(S, K, T, r, q, sigma, flag, *, vega: bool = True):
+    """Discounted Black-Scholes price and cash vega dV/dsigma; returns (V, vega or None)."""
+    dev = _device_of(S, K, T, r, q, sigma, flag)
+    s_, k, t, rr, qq, sg = (_on(a, dev, torch.float64) for a in (S, K, T, r, q, sigma))
+    fl = _on(flag, dev, torch.int8)
+    n = s_.numel()
+    _check_lengths(n, k, t, rr, qq, sg, fl)
+    V = torch.empty(n, dtype=torch.float64, device=dev)
+    vg = torch.empty(n, dtype=torch.float64, device=dev) if vega else None
+    _native.call("pivot_bs_price", n, _p(s_), _p(k), _p(t), _p(rr), _p(qq), _p(sg), _p(fl), _p(V), _p(vg),
+                 _stream(dev))
+    return tuple(_host_result((S, K, T, r, q, sigma, flag), [V, vg]))
+
+
+def bs_iv(S, K, T, r, q, V, flag, *, mode="fp64", householder: int = 0, status: bool = True):
+    """Implied volatility from the discounted price; returns (sigma, status or None)."""
+    dev = _device_of(S, K, T, r, q, V, flag)
+    s_, k, t, rr, qq, v = (_on(a, dev, torch.float64) for a in (S, K, T, r, q, V))
+    fl = _on(flag, dev, torch.int8)
+    n = s_.numel()
+    _check_lengths(n, k, t, rr, qq, v, fl)
+    sig = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev) if status else None
+    o = _opts(mode, householder)
+    _native.call("pivot_bs_iv_forward", n, _p(s_), _p(k), _p(t), _p(rr), _p(qq), _p(v), _p(fl), _p(sig), _p(st),
+                 ctypes.byref(o), _stream(dev))
+    return tuple(_host_result((S, K, T, r, q, V, flag), [sig, st]))
+
+
+def bs_iv_backward(S, K, T, r, q, flag, sigma, gbar=None, *, tau: float = 1e-6, gate="nan"):
+    """Gated VJP in xi; returns (dV, dS, dK, dT, dr, dq)."""
+    dev = _device_of(S, K, T, r, q, flag, sigma, gbar)
+    s_, k, t, rr, qq, sg = (_on(a, dev, torch.float64) for a in (S, K, T, r, q, sigma))
+    fl = _on(flag, dev, torch.int8)
+    g = _on(gbar, dev, torch.float64)
+    n = s_.numel()
+    _check_lengths(n, k, t, rr, qq, sg, fl, g)
+    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(6)]
+    _native.call("pivot_bs_iv_backward", n, _p(s_), _p(k), _p(t), _p(rr), _p(qq), _p(fl), _p(sg), _p(g),
+                 float(tau), _gate(gate), *[_p(o) for o in outs], _stream(dev))
+    return tuple(_host_result((S, K, T, r, q, flag, sigma, gbar), outs))
+
+
+def bs_iv_forward_backward(S, K, T, r, q, V, flag, gbar=None, *, tau: float = 1e-6, gate="nan", mode="fp64",
+                           householder: int = 0):
+    """Forward and gated adjoint in xi in one pass; returns (sigma, status, dV, dS, dK, dT, dr, dq)."""
+    dev = _device_of(S, K, T, r, q, V, flag, gbar)
+    s_, k, t, rr, qq, v = (_on(a, dev, torch.float64) for a in (S, K, T, r, q, V))
+    fl = _on(flag, dev, torch.int8)
+    g = _on(gbar, dev, torch.float64)
+    n = s_.numel()
+    _check_lengths(n, k, t, rr, qq, v, fl, g)
+    sig = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(6)]
+    o = _opts(mode, householder)
+    _native.call("pivot_bs_iv_forward_backward", n, _p(s_), _p(k), _p(t), _p(rr), _p(qq), _p(v), _p(fl), _p(g),
+                 float(tau), _gate(gate), _p(sig), _p(st), *[_p(x) for x in outs], ctypes.byref(o), _stream(dev))
+    return tuple(_host_result((S, K, T, r, q, V, flag, gbar), [sig, st, *outs]))
+
+
+class ImpliedVolBS(torch.autograd.Function):
+    """sigma = JaeckelIV(V; S, K, tau, r, q, flag) as an autograd node (Algorithm 1 on xi).
+
+    Saves (S, K, tau, r, q, flag, sigma) only; backward is the gated IFT VJP for V, S, K,
+    tau, r and q."""
+
+    @staticmethod
+    def forward(ctx, V, S, K, T, r, q, flag, tau=1e-6, gate="nan"):
+        sig, _ = bs_iv(S.detach(), K.detach(), T.detach(), r.detach(), q.detach(), V.detach(), flag, status=False)
+        ctx.save_for_backward(S.detach(), K.detach(), T.detach(), r.detach(), q.detach(), flag, sig)
+        ctx.tau, ctx.gate = float(tau), gate
+        return sig
+
+    @staticmethod
+    def backward(ctx, gsig):
+        S, K, T, r, q, flag, sig = ctx.saved_tensors
+        grads = bs_iv_backward(S, K, T, r, q, flag, sig, gsig.contiguous(), tau=ctx.tau, gate=ctx.gate)
+        need = ctx.needs_input_grad
+        return tuple(g if need[j] else None for j, g in enumerate(grads)) + (None, None, None)
+
+
+def bs_implied_volatility_autograd(V, S, K, T, r, q, flag, tau: float = 1e-6, gate="nan"):
+    """Differentiable implied volatility on xi = (S, K, tau, r, q), see ``ImpliedVolBS``."""
+    return ImpliedVolBS.apply(V, S, K, T, r, q, flag, tau, gate)

@@ -71,6 +71,36 @@ __global__ void __launch_bounds__(kBlock) k_iv_backward(int64_t n, const double*
   }
 }
 
+// Black-Scholes price on xi = (S, K, tau, r, q): e^{-r tau} B(S e^{(r-q) tau}, K, tau, sigma)
+// (Eq. app_black_scholes in forward coordinates, Eq. app_black76), and the cash vega.
+__global__ void __launch_bounds__(kBlock) k_bs_price(int64_t n, const double* __restrict__ S,
+                                                     const double* __restrict__ K, const double* __restrict__ T,
+                                                     const double* __restrict__ r, const double* __restrict__ q,
+                                                     const double* __restrict__ sigma,
+                                                     const int8_t* __restrict__ flag, double* __restrict__ V,
+                                                     double* __restrict__ vega) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double er, ec, p, v;
+    const double tau = T[i], rr = r[i];
+    pivot::bs_factors(tau, rr, q[i], er, ec);
+    pivot::black_price_row(S[i] * ec, K[i], tau, sigma[i], flag[i], p, v);
+    const double disc = exp(-rr * tau);
+    V[i] = disc * p;
+    if (vega) vega[i] = disc * v;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bs_iv_backward(Args a) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    double er, ec;
+    const double tau = a.T[i], rr = a.r[i], qq = a.q[i];
+    pivot::bs_factors(tau, rr, qq, er, ec);
+    write_grad_bs(a, i, a.F[i] * ec, a.K[i], tau, a.flag[i], a.sigma[i], rr, qq, er, ec);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Forward (and fused forward+backward) with per-tile compaction and region
 // binning.  A block owns a tile of kTile consecutive rows.
@@ -96,8 +126,26 @@ constexpr int kBins = 8;
 constexpr double kMixedFloor = 1e-30;
 constexpr double kMixedMaxAbsX = 80.0;
 constexpr size_t kBinnedSmem = size_t(kNodeFields) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
+// the Black-Scholes form keeps e^{r tau} and e^{(r-q) tau} of each row of the tile
+constexpr size_t kBinnedSmemBS = kBinnedSmem + 2 * kTile * sizeof(double);
 
-template <bool kBackward, bool kMixed>
+// Row inputs in forward coordinates.  The Black-Scholes form (kBS) reads the
+// spot S from a.F and the discounted price V from a.P and maps them with the
+// factors phase 1 left in shared memory; the products are the same in every
+// phase, so all phases see one F and one B.
+template <bool kBS>
+__device__ __forceinline__ void row_fp(const Args& a, int64_t i, int r, const double* s_er, const double* s_ec,
+                                       double& F, double& P) {
+  if (kBS) {
+    F = a.F[i] * s_ec[r];
+    P = a.P[i] * s_er[r];
+  } else {
+    F = a.F[i];
+    P = a.P[i];
+  }
+}
+
+template <bool kBackward, bool kMixed, bool kBS>
 __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
   extern __shared__ double smem[];
   double* s_x = smem;
@@ -106,8 +154,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
   double* s_bn = s_e + kTile;
   double* s_bsn = s_bn + kTile;
   double* s_bb = s_bsn + kTile;
-  uint16_t* s_list = reinterpret_cast<uint16_t*>(s_bb + kTile);  // phase 1 -> 2: rows to solve
-  uint16_t* s_order = s_list + kTile;                             // phase 2 -> 3: region order
+  double* s_er = s_bb + kTile;                     // kBS only
+  double* s_ec = s_er + (kBS ? kTile : 0);          // kBS only
+  uint16_t* s_list = reinterpret_cast<uint16_t*>(s_ec + (kBS ? kTile : 0));  // phase 1 -> 2: rows to solve
+  uint16_t* s_order = s_list + kTile;                                        // phase 2 -> 3: region order
   __shared__ int s_nsolve;
   __shared__ int s_cnt[kBins];
   __shared__ int s_off[kBins + 1];
@@ -125,13 +175,24 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
       const int64_t i = base + r;
       bool solve = false;
       if (i < a.n) {
-        const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
+        const double K = a.K[i], T = a.T[i];
+        double rr = 0.0, qq = 0.0;
+        if (kBS) {
+          rr = a.r[i];
+          qq = a.q[i];
+          pivot::bs_factors(T, rr, qq, s_er[r], s_ec[r]);
+        }
+        double F, P;
+        row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
         const int fl = a.flag[i];
         const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
         if (q.status != 0) {
           a.sigma[i] = q.sigma;
           if (a.status) a.status[i] = uint8_t(q.status);
-          if (kBackward) write_grad(a, i, F, K, T, fl, q.sigma);
+          if (kBackward) {
+            if (kBS) write_grad_bs(a, i, F, K, T, fl, q.sigma, rr, qq, s_er[r], s_ec[r]);
+            else write_grad(a, i, F, K, T, fl, q.sigma);
+          }
         } else {
           solve = true;
         }
@@ -151,7 +212,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
       if (qi < nsolve) {
         const int r = s_list[qi];
         const int64_t i = base + r;
-        const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
+        const double K = a.K[i], T = a.T[i];
+        double F, P;
+        row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
         const pivot::Quote q = pivot::classify_quote(F, K, T, P, a.flag[i]);
         double x, bmax;
         pivot::moneyness(F, K, x, bmax);
@@ -210,11 +273,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
 #pragma unroll
       for (int k = 1; k < kBins; ++k) bin += (qi >= s_off[k]) ? 1 : 0;
       const int64_t i = base + r;
-      const double F = a.F[i], K = a.K[i], T = a.T[i];
+      const double K = a.K[i], T = a.T[i];
+      double F, P;
+      row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
       const int fl = a.flag[i];
       const int rg = bin & 3;
       const double bb = s_bb[r];
-      const double lnbeta = (rg == pivot::kLower) ? pivot::log_beta(bb, F, K, T, a.P[i], fl) : 0.0;
+      const double lnbeta = (rg == pivot::kLower) ? pivot::log_beta(bb, F, K, T, P, fl) : 0.0;
       double s = 0.0;
       if (kMixed && bin < 4) {
         pivot::Node<float> nf;
@@ -227,13 +292,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
         s = pivot::solve_region_mixed(rg, nf, s_x[r], bb, lnbeta, a.steps);
         if (!(s > 0.0 && s < INFINITY)) {
           // float seed failed: redo the row in double from its inputs
-          const pivot::Quote q = pivot::classify_quote(F, K, T, a.P[i], fl);
+          const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
           double x, bmax;
           pivot::moneyness(F, K, x, bmax);
           const double rsq = rsqrt(F * K);
           pivot::Node<double> nd;
           const int rg2 = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
-          const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, a.P[i], fl) : 0.0;
+          const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, P, fl) : 0.0;
           s = pivot::solve_region<double>(rg2, nd, lnb2, a.steps);
         }
       } else {
@@ -254,13 +319,24 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
         // the adjoint at the solved s, reusing x and 1/sqrt(T) of this row
         const double g = a.gbar ? a.gbar[i] : 1.0;
         const double xs = (F >= K) ? -s_x[r] : s_x[r];
+        const double gate_tau = kBS ? a.tau * s_er[r] : a.tau;  // G_tau on the cash vega e^{-r tau} V
         const pivot::Grad d = isnan(g) ? pivot::degenerate_grad(true, g, a.mode)
                                        : pivot::adjoint_core(F, K, fl, sig, s, xs, inv_sqT, rsqrt(F * K), g,
-                                                             a.tau, a.mode);
-        if (a.dP) a.dP[i] = d.dP;
-        if (a.dF) a.dF[i] = d.dF;
-        if (a.dK) a.dK[i] = d.dK;
-        if (a.dT) a.dT[i] = d.dT;
+                                                             gate_tau, a.mode);
+        if (kBS) {
+          const pivot::BSGrad o = pivot::bs_grad(d, F, K, T, a.r[i], a.q[i], s_er[r], s_ec[r]);
+          if (a.dP) a.dP[i] = o.dV;
+          if (a.dF) a.dF[i] = o.dS;
+          if (a.dK) a.dK[i] = o.dK;
+          if (a.dT) a.dT[i] = o.dT;
+          if (a.dr) a.dr[i] = o.dr;
+          if (a.dq) a.dq[i] = o.dq;
+        } else {
+          if (a.dP) a.dP[i] = d.dP;
+          if (a.dF) a.dF[i] = d.dF;
+          if (a.dK) a.dK[i] = d.dK;
+          if (a.dT) a.dT[i] = d.dT;
+        }
       }
     }
     __syncthreads();
@@ -284,32 +360,27 @@ int check_opts(const pivot_opts* o, int* steps, int* mode) {
 }
 
 // persistent grid for the binned kernels: resident blocks x SMs, capped by the tiles
-template <bool kBackward, bool kMixed>
+template <bool kBackward, bool kMixed, bool kBS = false>
 int launch_binned(const Args& a, void* stream) {
+  // occupancy of this instantiation, looked up once per device
   static thread_local int configured_device = -1;
   static thread_local int blocks_per_sm = 0, num_sms = 0;
+  constexpr size_t smem = kBS ? kBinnedSmemBS : kBinnedSmem;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
   if (configured_device != dev) {
-    const void* fns[] = {reinterpret_cast<const void*>(k_iv_binned<false, false>),
-                         reinterpret_cast<const void*>(k_iv_binned<true, false>),
-                         reinterpret_cast<const void*>(k_iv_binned<false, true>),
-                         reinterpret_cast<const void*>(k_iv_binned<true, true>)};
-    int bmin = 1 << 30;
-    for (const void* f : fns) {
-      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBinnedSmem));
-      int b = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, kBinnedSmem);
-      bmin = b < bmin ? b : bmin;
-    }
+    const void* f = reinterpret_cast<const void*>(k_iv_binned<kBackward, kMixed, kBS>);
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, smem);
     cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    blocks_per_sm = bmin < 1 ? 1 : bmin;
+    blocks_per_sm = b < 1 ? 1 : b;
     configured_device = dev;
   }
   const int64_t tiles = (a.n + kTile - 1) / kTile;
   const int64_t cap = int64_t(blocks_per_sm) * num_sms;
   const unsigned grid = unsigned(tiles < cap ? tiles : cap);
-  k_iv_binned<kBackward, kMixed><<<grid, kBlock, kBinnedSmem, static_cast<cudaStream_t>(stream)>>>(a);
+  k_iv_binned<kBackward, kMixed, kBS><<<grid, kBlock, smem, static_cast<cudaStream_t>(stream)>>>(a);
   return launch_status();
 }
 
@@ -419,6 +490,94 @@ int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const
     return launch_learned(a, opts->mlp, opts->fallback, true, stream);
   }
   return mode == PIVOT_MODE_MIXED ? launch_binned<true, true>(a, stream) : launch_binned<true, false>(a, stream);
+}
+
+// ---- Black-Scholes interface on xi = (S, K, tau, r, q) ----------------------------------------
+
+int pivot_bs_price(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                   const double* q, const double* sigma, const int8_t* flag, double* V_out, double* vega_out,
+                   void* stream) {
+  if (n < 0) return PIVOT_E_SIZE;
+  if (n == 0) return PIVOT_OK;
+  int dev = -1;
+  const Ptr ps[] = {{S, true, true},      {K, true, true},         {T, true, true},         {r, true, true},
+                    {q, true, true},      {sigma, true, true},     {flag, true, false},     {V_out, true, true},
+                    {vega_out, false, true}};
+  int rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  k_bs_price<<<grid_for(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(n, S, K, T, r, q, sigma, flag, V_out,
+                                                                               vega_out);
+  return launch_status();
+}
+
+int pivot_bs_iv_forward(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                        const double* q, const double* V, const int8_t* flag, double* sigma_out,
+                        uint8_t* status_out, const pivot_opts* opts, void* stream) {
+  if (n < 0) return PIVOT_E_SIZE;
+  int steps, mode;
+  int rc = check_opts(opts, &steps, &mode);
+  if (rc != PIVOT_OK) return rc;
+  if (mode == PIVOT_MODE_LEARNED) return PIVOT_E_OPTS;
+  if (n == 0) return PIVOT_OK;
+  int dev = -1;
+  const Ptr ps[] = {{S, true, true},    {K, true, true},         {T, true, true},          {r, true, true},
+                    {q, true, true},    {V, true, true},         {flag, true, false},      {sigma_out, true, true},
+                    {status_out, false, false}};
+  rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  Args a{n, S, K, T, V, flag, nullptr, 0.0, 0, steps, sigma_out, status_out, nullptr, nullptr, nullptr, nullptr,
+         r, q, nullptr, nullptr};
+  return mode == PIVOT_MODE_MIXED ? launch_binned<false, true, true>(a, stream)
+                                  : launch_binned<false, false, true>(a, stream);
+}
+
+int pivot_bs_iv_backward(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                         const double* q, const int8_t* flag, const double* sigma, const double* gbar, double tau,
+                         int32_t gate_mode, double* dV, double* dS, double* dK, double* dT, double* dr, double* dq,
+                         void* stream) {
+  if (n < 0) return PIVOT_E_SIZE;
+  int rc = check_gate(tau, gate_mode);
+  if (rc != PIVOT_OK) return rc;
+  if (n == 0) return PIVOT_OK;
+  int dev = -1;
+  const Ptr ps[] = {{S, true, true},      {K, true, true},     {T, true, true},     {r, true, true},
+                    {q, true, true},      {flag, true, false}, {sigma, true, true}, {gbar, false, true},
+                    {dV, false, true},    {dS, false, true},   {dK, false, true},   {dT, false, true},
+                    {dr, false, true},    {dq, false, true}};
+  rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  Args a{n, S, K, T, nullptr, flag, gbar, tau, gate_mode, 0, const_cast<double*>(sigma), nullptr, dV, dS, dK, dT,
+         r, q, dr, dq};
+  k_bs_iv_backward<<<grid_for(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(a);
+  return launch_status();
+}
+
+int pivot_bs_iv_forward_backward(int64_t n, const double* S, const double* K, const double* T, const double* r,
+                                 const double* q, const double* V, const int8_t* flag, const double* gbar,
+                                 double tau, int32_t gate_mode, double* sigma_out, uint8_t* status_out, double* dV,
+                                 double* dS, double* dK, double* dT, double* dr, double* dq,
+                                 const pivot_opts* opts, void* stream) {
+  if (n < 0) return PIVOT_E_SIZE;
+  int steps, mode;
+  int rc = check_opts(opts, &steps, &mode);
+  if (rc == PIVOT_OK) rc = check_gate(tau, gate_mode);
+  if (rc != PIVOT_OK) return rc;
+  if (mode == PIVOT_MODE_LEARNED) return PIVOT_E_OPTS;
+  if (n == 0) return PIVOT_OK;
+  int dev = -1;
+  const Ptr ps[] = {{S, true, true},         {K, true, true},       {T, true, true},      {r, true, true},
+                    {q, true, true},         {V, true, true},       {flag, true, false},  {gbar, false, true},
+                    {sigma_out, true, true}, {status_out, false, false}, {dV, false, true}, {dS, false, true},
+                    {dK, false, true},       {dT, false, true},     {dr, false, true},    {dq, false, true}};
+  rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  Args a{n, S, K, T, V, flag, gbar, tau, gate_mode, steps, sigma_out, status_out, dV, dS, dK, dT, r, q, dr, dq};
+  return mode == PIVOT_MODE_MIXED ? launch_binned<true, true, true>(a, stream)
+                                  : launch_binned<true, false, true>(a, stream);
 }
 
 int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream) {

@@ -568,6 +568,44 @@ __device__ __forceinline__ Grad gated_adjoint(double F, double K, double T, int 
 }
 
 // ---------------------------------------------------------------------------
+// Black-Scholes form on xi = (S, K, tau, r, q) (Eq. app_forward_price,
+// Algorithm 1): F = S e^{(r-q) tau}, B = e^{r tau} V, then the Black-76 path.
+// er = e^{r tau} and ec = e^{(r-q) tau}; NaN for a non-finite r or q, which
+// makes F NaN and the row a bad input.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bs_factors(double tau, double r, double q, double& er, double& ec) {
+  if (isfinite(r) && isfinite(q)) {
+    er = exp(r * tau);
+    ec = exp((r - q) * tau);
+  } else {
+    er = ec = __longlong_as_double(0x7ff8000000000000LL);
+  }
+}
+
+struct BSGrad {
+  double dV, dS, dK, dT, dr, dq;
+};
+
+// The xi-gradient from the Black-76 one at F = S ec, B = er V: sigma depends on
+// (V, S, r, q) only through B and F, so dV = er dB and dS = ec dF; the rate and
+// dividend terms follow from homogeneity (F dF + K dK + B dB = 0):
+//   dr = tau (B dB + F dF) = -tau K dK,   dq = -tau F dF,
+//   dtau = dT + r B dB + (r - q) F dF = dT - q F dF - r K dK.
+// A zero rate or yield adds no term (keeps an infinite Mills ratio from making 0 inf).
+__device__ __forceinline__ BSGrad bs_grad(const Grad& d, double F, double K, double tau, double r, double q,
+                                          double er, double ec) {
+  BSGrad o;
+  const double fdF = F * d.dF, kdK = K * d.dK;
+  o.dV = d.dP * er;
+  o.dS = d.dF * ec;
+  o.dK = d.dK;
+  o.dr = -tau * kdK;
+  o.dq = -tau * fdF;
+  o.dT = d.dT - (q != 0.0 ? q * fdF : 0.0) - (r != 0.0 ? r * kdK : 0.0);
+  return o;
+}
+
+// ---------------------------------------------------------------------------
 // Black-76 price with r = 0: intrinsic + sqrt(FK) b(x, s), vega.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void black_price_row(double F, double K, double T, double sigma, int flag, double& P,

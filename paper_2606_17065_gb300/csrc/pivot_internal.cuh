@@ -25,6 +25,10 @@ struct Args {
   double* sigma;
   uint8_t* status;
   double *dP, *dF, *dK, *dT;
+  // Black-Scholes form only: F holds the spot S, P the discounted price V,
+  // dP / dF / dT receive dsigma/dV, dsigma/dS, dsigma/dtau; r, q per row
+  const double *r, *q;
+  double *dr, *dq;
 };
 
 __device__ __forceinline__ void write_grad(const Args& a, int64_t i, double F, double K, double T, int fl,
@@ -35,6 +39,20 @@ __device__ __forceinline__ void write_grad(const Args& a, int64_t i, double F, d
   if (a.dF) a.dF[i] = d.dF;
   if (a.dK) a.dK[i] = d.dK;
   if (a.dT) a.dT[i] = d.dT;
+}
+
+// Black-Scholes form: the gated adjoint of a finished row in xi coordinates
+__device__ __forceinline__ void write_grad_bs(const Args& a, int64_t i, double F, double K, double T, int fl,
+                                              double sig, double r, double q, double er, double ec) {
+  const double g = a.gbar ? a.gbar[i] : 1.0;
+  const pivot::Grad d = pivot::gated_adjoint(F, K, T, fl, sig, g, a.tau * er, a.mode);
+  const pivot::BSGrad o = pivot::bs_grad(d, F, K, T, r, q, er, ec);
+  if (a.dP) a.dP[i] = o.dV;
+  if (a.dF) a.dF[i] = o.dS;
+  if (a.dK) a.dK[i] = o.dK;
+  if (a.dT) a.dT[i] = o.dT;
+  if (a.dr) a.dr[i] = o.dr;
+  if (a.dq) a.dq[i] = o.dq;
 }
 
 // warp-aggregated append: returns this lane's slot in a shared counter
