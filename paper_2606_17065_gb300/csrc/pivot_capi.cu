@@ -195,6 +195,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
           }
         } else {
           solve = true;
+          // the time value and its complement, for phase 2 (their slots are free until then)
+          s_bb[r] = q.tv;
+          s_e[r] = q.cv;
         }
       }
       const int slot = warp_append(solve, &s_nsolve, lane);
@@ -212,14 +215,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
       if (qi < nsolve) {
         const int r = s_list[qi];
         const int64_t i = base + r;
-        const double K = a.K[i], T = a.T[i];
-        double F, P;
-        row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
-        const pivot::Quote q = pivot::classify_quote(F, K, T, P, a.flag[i]);
+        const double K = a.K[i];
+        const double F = kBS ? a.F[i] * s_ec[r] : a.F[i];
         double x, bmax;
         pivot::moneyness(F, K, x, bmax);
         const double rsq = rsqrt(F * K);
-        const double beta = q.tv * rsq, betac = q.cv * rsq;
+        const double beta = s_bb[r] * rsq, betac = s_e[r] * rsq;
         bool fp64_row = true;
         if (kMixed && beta > kMixedFloor && betac > kMixedFloor && x > -kMixedMaxAbsX) {
           // float node and region; the float copies are exact in double storage
@@ -227,12 +228,14 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
           rg = pivot::classify<float>(float(x), float(bmax), float(beta), float(betac), nf);
           if (nf.bsn > 0.0f && nf.bn >= 0.0f) {
             fp64_row = false;
+            // x, b_max and beta (or beta_c) in double for the final FP64 step and the
+            // adjoint; the float node packed two floats to a slot (no conversions)
             s_x[r] = x;
-            s_bmax[r] = double(nf.bmax);
-            s_e[r] = double(nf.e);
-            s_bn[r] = double(nf.bn);
-            s_bsn[r] = double(nf.bsn);
+            s_bmax[r] = bmax;
             s_bb[r] = (rg == pivot::kUpper) ? betac : beta;
+            *reinterpret_cast<float2*>(&s_e[r]) = make_float2(nf.e, nf.bn);
+            *reinterpret_cast<float2*>(&s_bn[r]) = make_float2(nf.bsn, nf.x);
+            *reinterpret_cast<float2*>(&s_bsn[r]) = make_float2(nf.bmax, nf.bb);
           }
         }
         if (fp64_row) {
@@ -281,15 +284,19 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
       const double bb = s_bb[r];
       const double lnbeta = (rg == pivot::kLower) ? pivot::log_beta(bb, F, K, T, P, fl) : 0.0;
       double s = 0.0;
+      pivot::Last last;
       if (kMixed && bin < 4) {
         pivot::Node<float> nf;
-        nf.x = float(s_x[r]);
-        nf.bmax = float(s_bmax[r]);
-        nf.e = float(s_e[r]);
-        nf.bn = float(s_bn[r]);
-        nf.bsn = float(s_bsn[r]);
-        nf.bb = float(bb);
-        s = pivot::solve_region_mixed(rg, nf, s_x[r], bb, lnbeta, a.steps);
+        const float2 p0 = *reinterpret_cast<const float2*>(&s_e[r]);
+        const float2 p1 = *reinterpret_cast<const float2*>(&s_bn[r]);
+        const float2 p2 = *reinterpret_cast<const float2*>(&s_bsn[r]);
+        nf.e = p0.x;
+        nf.bn = p0.y;
+        nf.bsn = p1.x;
+        nf.x = p1.y;
+        nf.bmax = p2.x;
+        nf.bb = p2.y;
+        s = pivot::solve_mixed64(rg, nf, s_x[r], s_bmax[r], bb, lnbeta, a.steps, last);
         if (!(s > 0.0 && s < INFINITY)) {
           // float seed failed: redo the row in double from its inputs
           const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
           pivot::Node<double> nd;
           const int rg2 = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
           const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, P, fl) : 0.0;
-          s = pivot::solve_region<double>(rg2, nd, lnb2, a.steps);
+          s = pivot::solve64(rg2, nd, lnb2, a.steps, last);
         }
       } else {
         pivot::Node<double> nd;
@@ -309,7 +316,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
         nd.bn = s_bn[r];
         nd.bsn = s_bsn[r];
         nd.bb = bb;
-        s = pivot::solve_region<double>(rg, nd, lnbeta, a.steps);
+        s = pivot::solve64(rg, nd, lnbeta, a.steps, last);
       }
       const double inv_sqT = rsqrt(T);
       const double sig = s * inv_sqT;
@@ -318,11 +325,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
       if (kBackward) {
         // the adjoint at the solved s, reusing x and 1/sqrt(T) of this row
         const double g = a.gbar ? a.gbar[i] : 1.0;
-        const double xs = (F >= K) ? -s_x[r] : s_x[r];
         const double gate_tau = kBS ? a.tau * s_er[r] : a.tau;  // G_tau on the cash vega e^{-r tau} V
         const pivot::Grad d = isnan(g) ? pivot::degenerate_grad(true, g, a.mode)
-                                       : pivot::adjoint_core(F, K, fl, sig, s, xs, inv_sqT, rsqrt(F * K), g,
-                                                             gate_tau, a.mode);
+                                       : pivot::adjoint_reuse(F, K, fl, sig, s, s_x[r], s_bmax[r], inv_sqT,
+                                                              rsqrt(F * K), g, gate_tau, a.mode, last);
         if (kBS) {
           const pivot::BSGrad o = pivot::bs_grad(d, F, K, T, a.r[i], a.q[i], s_er[r], s_ec[r]);
           if (a.dP) a.dP[i] = o.dV;

@@ -211,10 +211,27 @@ __device__ __forceinline__ R shape_monotone(R D, R y0, R y1, R d0, R d1) {
 // Row preparation (Algorithm 1 forward normalisation with r = 0; appendix
 // stages 1-2).
 // ---------------------------------------------------------------------------
+// Sign and class tests on the bit pattern: integer instructions, which leave
+// the FP64 pipe (2 lanes per cycle per SM on this part) to the arithmetic.
+// positive, finite and non-zero: bits - 1 < bits(+inf) - 1 as unsigned
+__device__ __forceinline__ bool pos_finite(double v) {
+  return uint64_t(__double_as_longlong(v)) - 1ull < 0x7fefffffffffffffull;
+}
+__device__ __forceinline__ bool finite64(double v) {
+  return (uint64_t(__double_as_longlong(v)) & 0x7fffffffffffffffull) < 0x7ff0000000000000ull;
+}
+// v < 0 for a non-NaN v (-0 is not negative)
+__device__ __forceinline__ bool neg64(double v) {
+  return uint64_t(__double_as_longlong(v)) > 0x8000000000000000ull;
+}
+// v == 0 (either sign)
+__device__ __forceinline__ bool zero64(double v) { return (uint64_t(__double_as_longlong(v)) << 1) == 0ull; }
+// a > b for positive finite a, b: their bit patterns order as integers
+__device__ __forceinline__ bool gt_pos(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
+
 __device__ __forceinline__ bool bad_inputs(double F, double K, double T, int flag) {
   // also rejects NaN and +-inf
-  return !(F > 0.0 && F < INFINITY) || !(K > 0.0 && K < INFINITY) || !(T > 0.0 && T < INFINITY) ||
-         (flag != 1 && flag != -1);
+  return !pos_finite(F) || !pos_finite(K) || !pos_finite(T) || (flag != 1 && flag != -1);
 }
 
 // P - F + K (call) or P - K + F (put) with two error-free TwoSums, one rounding
@@ -262,19 +279,19 @@ __device__ __forceinline__ Quote classify_quote(double F, double K, double T, do
   q.tv = q.cv = 0.0;
   q.status = 0;
   q.sigma = 0.0;
-  if (bad_inputs(F, K, T, flag) || !(fabs(P) < INFINITY)) {
+  if (bad_inputs(F, K, T, flag) || !finite64(P)) {
     q.status = 3;
     q.sigma = qnan;
     return q;
   }
   const bool call = flag > 0;
-  const bool itm = call ? (F > K) : (K > F);
+  const bool itm = call ? gt_pos(F, K) : gt_pos(K, F);
   q.tv = itm ? (call ? time_value_itm(P, F, K) : time_value_itm(P, K, F)) : P;
   q.cv = (call ? F : K) - P;
-  if (q.tv < 0.0) { q.status = 1; q.sigma = qnan; }
-  else if (q.cv < 0.0) { q.status = 2; q.sigma = qnan; }
-  else if (q.tv == 0.0) { q.status = 4; q.sigma = 0.0; }
-  else if (q.cv == 0.0) { q.status = 5; q.sigma = INFINITY; }
+  if (neg64(q.tv)) { q.status = 1; q.sigma = qnan; }
+  else if (neg64(q.cv)) { q.status = 2; q.sigma = qnan; }
+  else if (zero64(q.tv)) { q.status = 4; q.sigma = 0.0; }
+  else if (zero64(q.cv)) { q.status = 5; q.sigma = INFINITY; }
   return q;
 }
 
@@ -445,6 +462,115 @@ __device__ __forceinline__ R householder_step(R x, R beta, R lnbetac, R inv_lnbe
   return s + num / den;
 }
 
+// ---------------------------------------------------------------------------
+// The FP64 Householder(3) step of the binned kernels.  Same objectives as
+// householder_step<double>, evaluated through the two Mills ratios of
+// non-positive argument only (one table evaluation each, no exponential):
+//   ya = Y(-|h + t|),  yb = Y(h - t)   (h - t < 0 always)
+// and the reflection Y(z) + Y(-z) = 1/phi(z), which at z = h + t reads
+//   Y(h + t) + Y(-h - t) = b_max / b_s = E1          (e^{x/2} phi(h+t) = b_s)
+// so the larger ratio costs one multiply once 1/b_s is known:
+//   rho   = ya - yb            (h + t <= 0),  E1 - ya - yb   (h + t > 0)
+//   gamma = ya + yb            (h + t > 0),   E1 - ya + yb   (h + t <= 0)
+// (the same cancellation as Y(h+t) - Y(h-t) itself).  The middle objective's
+// Newton ratio nu = (beta - b)/b_s = beta / b_s - rho takes 1/b_s = exp(-ln b_s)
+// once.  The step records where it evaluated (z_a = -|h + t|, z_b = h - t)
+// and the two ratios, so that the adjoint at the final iterate needs no new
+// Mills ratio (adjoint_reuse).
+// kF32Ratios: the derivative ratios h2, h3 of the step (and those of b) in
+// float.  For the last step of the mixed form, whose iterate is within ~1e-6
+// relative, they only enter through nu (h2 nu / 2 + ...) ~ nu^2: their float
+// rounding moves s by ~1e-7 nu^2, below double rounding.  nu itself, the
+// residual, stays double.
+// ---------------------------------------------------------------------------
+struct Last {
+  double za, zb; // arguments of the two Mills ratios at the last evaluation
+  double ya, yb; // Y(za), Y(zb)
+  bool pair;     // false: the Taylor zone of rho evaluated neither
+};
+
+// Y(z) for z <= 0: no reflection branch
+static __device__ __noinline__ double mills_small(double z) { return kSqrtPiOver2 * erfcx_nonneg(-z * kInvSqrt2); }
+
+template <bool kF32Ratios>
+__device__ __forceinline__ double step64(double x, double bmax, double beta, double lnbetac, double inv_lnbeta,
+                                         int region, double s, Last& last) {
+  const double inv_s = 1.0 / s;
+  const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
+  const double lbs = log_bs<double>(h, t);
+  const bool taylor = region != kUpper && t <= kTaylorT && x >= -kTaylorX;
+  last.za = -fabs(hpt);
+  last.zb = h - t;
+  last.pair = !taylor;
+  double ya = 0.0, yb = 0.0;
+  if (!taylor) {
+    ya = mills_small(last.za);
+    yb = mills_small(last.zb);
+  }
+  last.ya = ya;
+  last.yb = yb;
+  // 1/b_s where the middle objective or the larger ratio of the pair needs it
+  const bool need_ibs = region == kMidLow || region == kMidHigh || (region == kLower ? hpt > 0.0 : hpt <= 0.0);
+  double ibs = need_ibs ? exp(-lbs) : 0.0;
+  double E1 = bmax * ibs;
+  double beta_ibs = beta * ibs;
+  if (!(ibs < INFINITY)) {
+    // b_s below ~1e-308 (|ln(F/K)| beyond ~1400): the products in logarithms
+    E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
+    beta_ibs = exp(log(beta) - lbs);
+  }
+  double nu, L = 0.0, q = 0.0;
+  if (region == kUpper) {
+    const double gam = (hpt > 0.0) ? ya + yb : (E1 - ya) + yb;
+    q = 1.0 / gam;
+    nu = -(lnbetac - lbs - log(gam)) * gam;
+  } else {
+    const double rho = taylor ? rho_taylor<double>(h, t) : (hpt <= 0.0 ? ya - yb : (E1 - ya) - yb);
+    if (region == kLower) {
+      L = lbs + log(rho); // ln b
+      q = 1.0 / rho;
+      nu = rho * L * (1.0 - L * inv_lnbeta);
+    } else {
+      nu = beta_ibs - rho;
+    }
+  }
+  if (kF32Ratios) {
+    const float fis = float(inv_s), fh = float(h), ft = float(t), fhh = fh * fh;
+    const float b2 = (fhh - ft * ft) * fis;
+    const float b3 = fmaf(b2, b2, -3.0f * fhh * fis * fis) - 0.25f;
+    float h2 = b2, h3 = b3;
+    const float fq = float(q);
+    if (region == kLower) {
+      const float iL = 1.0f / float(L);
+      h2 = b2 - fq * fmaf(2.0f, iL, 1.0f);
+      h3 = b3 - 3.0f * b2 * fq + 2.0f * fq * fq - 6.0f * fq * (b2 - fq) * iL + 6.0f * fq * fq * iL * iL;
+    } else if (region == kUpper) {
+      h2 = b2 + fq;
+      h3 = b3 + 3.0f * fq * b2 + 2.0f * fq * fq;
+    }
+    // (1 + h2 nu/2) / (1 + nu (h2 + h3 nu/6)) - 1 = -nu (h2/2 + h3 nu/6) / (1 + nu (h2 + h3 nu/6))
+    const float fnu = float(nu);
+    const float a = fmaf(h3 * (1.0f / 6.0f), fnu, h2);
+    const float corr = -fnu * fmaf(h3 * (1.0f / 6.0f), fnu, 0.5f * h2) / fmaf(fnu, a, 1.0f);
+    return s + fma(nu, double(corr), nu);
+  }
+  const double hh = h * h;
+  const double b2 = (hh - t * t) * inv_s;
+  const double b3 = fma(b2, b2, -3.0 * hh * inv_s * inv_s) - 0.25;
+  double h2 = b2, h3 = b3;
+  if (region == kLower) {
+    const double iL = 1.0 / L;
+    h2 = b2 - q * fma(2.0, iL, 1.0);
+    h3 = b3 - 3.0 * b2 * q + 2.0 * q * q - 6.0 * q * (b2 - q) * iL + 6.0 * q * q * iL * iL;
+  } else if (region == kUpper) {
+    h2 = b2 + q;
+    h3 = b3 + 3.0 * q * b2 + 2.0 * q * q;
+  }
+  const double num = nu * fma(0.5 * h2, nu, 1.0);
+  const double den = fma(nu, fma(h3 * (1.0 / 6.0), nu, h2), 1.0);
+  return s + num / den;
+}
+
 // Guess plus `steps` Householder(3) steps for a classified row; returns s.
 template <typename R>
 __device__ __forceinline__ R solve_region(int region, const Node<R>& nd, R lnbeta, int steps) {
@@ -453,6 +579,30 @@ __device__ __forceinline__ R solve_region(int region, const Node<R>& nd, R lnbet
   R s = region_guess<R>(region, nd, lnbeta);
   for (int i = 0; i < steps; ++i) s = householder_step<R>(nd.x, nd.bb, lnbetac, inv_lnbeta, region, s);
   return s;
+}
+
+// The FP64 solve of the binned kernels: guess plus `steps` step64 steps; the
+// last step's Mills ratios are left in `last` for adjoint_reuse.
+__device__ __forceinline__ double solve64(int region, const Node<double>& nd, double lnbeta, int steps, Last& last) {
+  const double lnbetac = (region == kUpper) ? log(nd.bb) : 0.0;
+  const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
+  double s = region_guess<double>(region, nd, lnbeta);
+  for (int i = 0; i < steps; ++i) s = step64<false>(nd.x, nd.bmax, nd.bb, lnbetac, inv_lnbeta, region, s, last);
+  return s;
+}
+
+// The mixed solve of the binned kernels: float guess and `steps - 1` float
+// steps, then one step64 with float derivative ratios from the float iterate
+// (x, bmax, bb and lnbeta in double).
+__device__ __forceinline__ double solve_mixed64(int region, const Node<float>& nf, double x, double bmax, double bb,
+                                                double lnbeta, int steps, Last& last) {
+  const float lnbetac_f = (region == kUpper) ? logf(nf.bb) : 0.0f;
+  const float inv_lnbeta_f = (region == kLower) ? 1.0f / float(lnbeta) : 0.0f;
+  float sf = region_guess<float>(region, nf, float(lnbeta));
+  for (int i = 1; i < steps; ++i) sf = householder_step<float>(nf.x, nf.bb, lnbetac_f, inv_lnbeta_f, region, sf);
+  const double lnbetac = (region == kUpper) ? log(bb) : 0.0;
+  const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
+  return step64<true>(x, bmax, bb, lnbetac, inv_lnbeta, region, double(sf), last);
 }
 
 // Mixed precision (PIVOT_MODE_MIXED): the float node seeds a float guess and
@@ -546,6 +696,94 @@ __device__ __forceinline__ Grad adjoint_core(double F, double K, int flag, doubl
   } else {
     const double inv_tau = 1.0 / tau;
     const double r = V * inv_tau;
+    const double den = 1.0 / fma(r, r, 1.0);
+    w = r * r * den;
+    wP = r * inv_tau * den;
+  }
+  out.dP = g * wP;
+  out.dF = g * jF * w;
+  out.dK = g * jK * w;
+  out.dT = g * jT * w;
+  return out;
+}
+
+// Y(z0 + d) to second order from Y(z0): Y' = 1 + zY, Y'' = z + (1 + z^2) Y.
+// |d| <~ 1e-5 |z0| at the final iterate of every solve, so the third-order
+// term (Y''' d^3 / 6, relative ~ d^3 / |z|^3 for z < 0) is below 1e-15.
+__device__ __forceinline__ double mills_shift(double y0, double z0, double d) {
+  const double y1 = fma(z0, y0, 1.0);
+  const double y2 = fma(fma(z0, z0, 1.0), y0, z0);
+  return fma(fma(0.5 * y2, d, y1), d, y0);
+}
+
+// The gated adjoint of a solved row (as adjoint_core) at its final s, with the
+// Mills ratios carried from the last Householder evaluation (`last`) instead
+// of evaluated anew.  x = -|ln(F/K)|, bmax = e^{x/2}.  With h = x/s, t = s/2,
+// E1 = b_max / b_s and E2 = 1 / (b_max b_s) (1/phi(h + t) and 1/phi(h - t)):
+//   Y(h + t), Y(-h - t): one is ya, the other E1 - ya
+//   Y(h - t) = yb,  Y(t - h) = E2 - yb
+// and the four quote types need (theta = flag):
+//   F <= K: d1 = h + t, d2 = h - t;  F > K: d1 = t - h, d2 = -(h + t);
+//   dsigma/dF uses Y(theta d1), dsigma/dK uses Y(theta d2).
+// 1/V = (1/b_s) rsq / sqrt(T) needs no division.
+__device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, double sigma, double s, double x,
+                                              double bmax, double inv_sqT, double rsq, double g, double tau, int mode,
+                                              const Last& last) {
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  const double inv_s = 1.0 / s;
+  const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
+  const double za = -fabs(hpt), zb = h - t;
+  // the shift is used while it is small (|d| < 1e-4 (1 + |z|): third-order term < 1e-12)
+  const bool near = last.pair && fabs(za - last.za) < 1e-4 * (1.0 - za) && fabs(zb - last.zb) < 1e-4 * (1.0 - zb);
+  const double ya = near ? mills_shift(last.ya, last.za, za - last.za) : mills_small(za);
+  const double yb = near ? mills_shift(last.yb, last.zb, zb - last.zb) : mills_small(zb);
+  const double lbs = log_bs<double>(h, t);
+  double ibs = exp(-lbs), E1 = bmax * ibs, E2 = ibs / bmax;
+  if (!finite64(ibs)) {
+    // b_s underflows (|ln(F/K)| beyond ~1400): the reflections from their own exponents
+    E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
+    E2 = kSqrt2Pi * exp(0.5 * zb * zb);
+  }
+  const double y_hpt = hpt <= 0.0 ? ya : E1 - ya;  // Y(h + t)
+  const double y_mhpt = hpt <= 0.0 ? E1 - ya : ya; // Y(-h - t)
+  const bool call = flag > 0, fle = F <= K;
+  const bool itm = call ? !fle : fle;
+  const double y_tmh = itm ? E2 - yb : 0.0; // Y(t - h), in-the-money quotes only
+  const double u1 = fle ? (call ? y_hpt : y_mhpt) : (call ? y_tmh : yb);  // Y(theta d1)
+  const double u2 = fle ? (call ? yb : y_tmh) : (call ? y_mhpt : y_hpt);  // Y(theta d2)
+  const double sg = call ? 1.0 : -1.0;
+  const double rsq2 = rsq * rsq;
+  const double jP = ibs * rsq * inv_sqT; // 1/V, V = b_s sqrt(F K) sqrt(T)
+  const double jF = -sg * u1 * (K * rsq2) * inv_sqT;
+  const double jK = sg * u2 * (F * rsq2) * inv_sqT;
+  const double jT = -0.5 * sigma * inv_sqT * inv_sqT;
+  Grad out;
+  const bool in_g = tau * jP < 1.0; // V > tau
+  if (mode == 0 || (mode <= 2 && in_g)) {
+    out.dP = g * jP;
+    out.dF = g * jF;
+    out.dK = g * jK;
+    out.dT = g * jT;
+    return out;
+  }
+  if (mode == 1) {
+    const double v = (g == 0.0) ? 0.0 : qnan;
+    out.dP = out.dF = out.dK = out.dT = v;
+    return out;
+  }
+  if (mode == 2) {
+    out.dP = out.dF = out.dK = out.dT = 0.0;
+    return out;
+  }
+  // smooth gate w = V^2/(V^2 + tau^2); w/V = V/(V^2 + tau^2)
+  double w, wP;
+  if (in_g) {
+    const double r = tau * jP;
+    w = 1.0 / fma(r, r, 1.0);
+    wP = w * jP;
+  } else {
+    const double inv_tau = 1.0 / tau;
+    const double r = 1.0 / (tau * jP); // V / tau
     const double den = 1.0 / fma(r, r, 1.0);
     w = r * r * den;
     wP = r * inv_tau * den;

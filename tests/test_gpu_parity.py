@@ -306,3 +306,30 @@ def test_mills_ratio_fp64_erfcx():
     rel = np.abs(y[fin] - ref[fin]) / ref[fin]
     assert np.all(rel <= tol[fin]), rel.max()
     assert y[z == -np.inf][0] == 0.0 and np.isinf(y[z == np.inf][0])
+
+
+def test_extreme_moneyness():
+    """|ln(F/K)| from 50 to 1400 (b_max down to e^-700): the reflections through 1/b_s and the
+    adjoint's large Mills ratios stay finite where the exact values are."""
+    F, K, T, S, flag = [], [], [], [], []
+    for ax in (50.0, 300.0, 690.0, 1000.0, 1400.0):
+        sc = np.sqrt(2 * ax)
+        for sfac in (0.6, 0.9, 1.0, 1.1, 1.5):
+            for fl in (1, -1):
+                for side in (1, -1):
+                    f = np.exp(side * ax / 2)
+                    F.append(f); K.append(1.0 / f); T.append(1.0); S.append(sfac * sc); flag.append(fl)
+    F, K, T, S = map(np.array, (F, K, T, S))
+    flag = np.array(flag, np.int8)
+    P, _ = oracle.black_price(F, K, T, S, flag)
+    ref, st_ref = oracle.implied_vol(F, K, T, P, flag)
+    assert (st_ref == 0).sum() >= 24  # in-the-money rows collapse onto a bound at these scales
+    sig, st = pv.iv(to_dev(F), to_dev(K), to_dev(T), to_dev(P), to_dev(flag))
+    sig, st = to_np(sig), to_np(st)
+    dom = assert_sigma_parity(F, K, T, P, flag, sig, st, ref, st_ref, where="extreme")
+    for mode in (0, 1):
+        out = pv.iv_forward_backward(to_dev(F), to_dev(K), to_dev(T), to_dev(P), to_dev(flag), tau=1e-300,
+                                     gate=mode)
+        want = oracle.iv_grad(F, K, T, flag, ref, None, 1e-300, mode)
+        _, Vr = oracle.black_price(F, K, T, np.where(np.isfinite(ref), ref, 1.0), flag)
+        assert_grad_parity([to_np(x) for x in out[2:]], want, dom, where=f"extreme mode={mode}", vega=Vr)
