@@ -116,18 +116,25 @@ __global__ void __launch_bounds__(kBlock) k_bs_iv_backward(Args a) {
 //           boundary diverge.  sigma and the gated adjoint are written here.
 // The grid is persistent: blocks stride over tiles.
 // ---------------------------------------------------------------------------
-constexpr int kTile = 1024;
-constexpr int kRowsPerThread = kTile / kBlock;
-constexpr int kNodeFields = 6;
+// Tile rows per block: 2,048 for the Black-76 forms (2 blocks of 256 threads
+// per SM, 106,496 B of shared memory each), 1,024 for the Black-Scholes form,
+// whose two extra doubles per row would not let two 2,048-row blocks fit
+// (3 blocks of 69,632 B).  Larger tiles pack the region bins of phase 3 into
+// fewer partially filled warps.
+template <bool kBS>
+struct TileCfg {
+  static constexpr int kTile = kBS ? 1024 : 2048;
+  static constexpr int kMinBlocks = kBS ? 3 : 2;
+  static constexpr int kRowsPerThread = kTile / kBlock;
+  // six node fields per row (+ e^{r tau}, e^{(r-q) tau} in the Black-Scholes form), two row lists
+  static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
+};
 // mixed mode: 4 float-seeded region bins plus 4 FP64 bins for rows outside
 // the float range (beta or b_max - beta below kMixedFloor, or |x| above
 // kMixedMaxAbsX, where the float node would underflow)
 constexpr int kBins = 8;
 constexpr double kMixedFloor = 1e-30;
 constexpr double kMixedMaxAbsX = 80.0;
-constexpr size_t kBinnedSmem = size_t(kNodeFields) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
-// the Black-Scholes form keeps e^{r tau} and e^{(r-q) tau} of each row of the tile
-constexpr size_t kBinnedSmemBS = kBinnedSmem + 2 * kTile * sizeof(double);
 
 // Row inputs in forward coordinates.  The Black-Scholes form (kBS) reads the
 // spot S from a.F and the discounted price V from a.P and maps them with the
@@ -146,7 +153,9 @@ __device__ __forceinline__ void row_fp(const Args& a, int64_t i, int r, const do
 }
 
 template <bool kBackward, bool kMixed, bool kBS>
-__global__ void __launch_bounds__(kBlock, 3) k_iv_binned(Args a) {
+__global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(Args a) {
+  constexpr int kTile = TileCfg<kBS>::kTile;
+  constexpr int kRowsPerThread = TileCfg<kBS>::kRowsPerThread;
   extern __shared__ double smem[];
   double* s_x = smem;
   double* s_bmax = s_x + kTile;
@@ -371,7 +380,8 @@ int launch_binned(const Args& a, void* stream) {
   // occupancy of this instantiation, looked up once per device
   static thread_local int configured_device = -1;
   static thread_local int blocks_per_sm = 0, num_sms = 0;
-  constexpr size_t smem = kBS ? kBinnedSmemBS : kBinnedSmem;
+  constexpr size_t smem = TileCfg<kBS>::kSmem;
+  constexpr int kTile = TileCfg<kBS>::kTile;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
   if (configured_device != dev) {
