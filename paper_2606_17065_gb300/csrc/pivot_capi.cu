@@ -291,7 +291,9 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
       const int fl = a.flag[i];
       const int rg = bin & 3;
       const double bb = s_bb[r];
-      const double lnbeta = (rg == pivot::kLower) ? pivot::log_beta(bb, F, K, T, P, fl) : 0.0;
+      // ln beta for the FP64 solve of a lower-region row (the float-seeded rows of the mixed form do without)
+      const double lnbeta =
+          (rg == pivot::kLower && !(kMixed && bin < 4)) ? pivot::log_beta(bb, F, K, T, P, fl) : 0.0;
       double s = 0.0;
       pivot::Last last;
       if (kMixed && bin < 4) {
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
         nf.x = p1.y;
         nf.bmax = p2.x;
         nf.bb = p2.y;
-        s = pivot::solve_mixed64(rg, nf, s_x[r], s_bmax[r], bb, lnbeta, a.steps, last);
+        s = pivot::solve_mixed64(rg, nf, s_x[r], s_bmax[r], bb, a.steps, last);
         if (!(s > 0.0 && s < INFINITY)) {
           // float seed failed: redo the row in double from its inputs
           const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);

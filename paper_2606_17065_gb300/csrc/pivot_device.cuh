@@ -486,6 +486,8 @@ __device__ __forceinline__ R householder_step(R x, R beta, R lnbetac, R inv_lnbe
 struct Last {
   double za, zb; // arguments of the two Mills ratios at the last evaluation
   double ya, yb; // Y(za), Y(zb)
+  double lbs;    // ln b_s there
+  double ibs;    // 1/b_s there, or 0 when the step did not form it
   bool pair;     // false: the Taylor zone of rho evaluated neither
 };
 
@@ -509,6 +511,8 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   }
   last.ya = ya;
   last.yb = yb;
+  last.lbs = lbs;
+  last.ibs = 0.0;
   // 1/b_s where the middle objective or the larger ratio of the pair needs it
   const bool need_ibs = region == kMidLow || region == kMidHigh || (region == kLower ? hpt > 0.0 : hpt <= 0.0);
   double ibs = need_ibs ? exp(-lbs) : 0.0;
@@ -581,6 +585,67 @@ __device__ __forceinline__ R solve_region(int region, const Node<R>& nd, R lnbet
   return s;
 }
 
+// The final FP64 step of the mixed form.  Its iterate comes from the float
+// solve (within ~1e-6 relative), so every region takes the Newton ratio of
+// f = b - beta, written without logarithms (beta and beta_c exact in double):
+//   nu = (beta - b) / b_s = beta / b_s - rho                 (lower, middle)
+//      = gamma - beta_c / b_s                                (upper, b_max - b = b_s gamma)
+// and the Householder(3) factor of b itself (h2 = b''/b', h3 = b'''/b') in
+// float from the float iterate: it enters as nu^2 (h2/2 + h3 nu/6) ~ 1e-12 s,
+// so float rounding there is below double rounding of s.  Near the lower tail
+// b'' / b' ~ x^2/s^3 is large, but the quartic error constant ~ (x^2/s^2)^3
+// times (1e-6)^4 stays far below 1e-16 wherever beta is a normal number.
+// Also records 1/b_s at s (ibs) for adjoint_reuse.
+__device__ __forceinline__ double step64_final(double x, double bmax, double bb, int region, double s, float sf,
+                                               float xf, Last& last) {
+  const double inv_s = 1.0 / s;
+  const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
+  const double lbs = log_bs<double>(h, t);
+  const bool taylor = region != kUpper && t <= kTaylorT && x >= -kTaylorX;
+  last.za = -fabs(hpt);
+  last.zb = h - t;
+  last.pair = !taylor;
+  double ya = 0.0, yb = 0.0;
+  if (!taylor) {
+    ya = mills_small(last.za);
+    yb = mills_small(last.zb);
+  }
+  last.ya = ya;
+  last.yb = yb;
+  double ibs = exp(-lbs);
+  double nu;
+  if (finite64(ibs)) {
+    const double E1 = bmax * ibs;
+    if (region == kUpper) {
+      const double gam = (hpt > 0.0) ? ya + yb : (E1 - ya) + yb;
+      nu = gam - bb * ibs;
+    } else {
+      const double rho = taylor ? rho_taylor<double>(h, t) : (hpt <= 0.0 ? ya - yb : (E1 - ya) - yb);
+      nu = bb * ibs - rho;
+    }
+  } else {
+    // b_s below the normal range (subnormal beta, or |ln(F/K)| beyond ~1400): in logarithms
+    const double E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
+    if (region == kUpper) {
+      const double gam = (hpt > 0.0) ? ya + yb : (E1 - ya) + yb;
+      nu = gam - exp(log(bb) - lbs);
+    } else {
+      const double rho = taylor ? rho_taylor<double>(h, t) : (hpt <= 0.0 ? ya - yb : (E1 - ya) - yb);
+      nu = exp(log(bb) - lbs) - rho;
+    }
+    ibs = 0.0; // not usable by the adjoint
+  }
+  last.lbs = lbs;
+  last.ibs = ibs;
+  const float fis = 1.0f / sf, fh = xf * fis, ft = 0.5f * sf, fhh = fh * fh;
+  const float b2 = (fhh - ft * ft) * fis;
+  const float b3 = fmaf(b2, b2, -3.0f * fhh * fis * fis) - 0.25f;
+  const float fnu = float(nu);
+  const float a = fmaf(b3 * (1.0f / 6.0f), fnu, b2);
+  const float corr = -fnu * fmaf(b3 * (1.0f / 6.0f), fnu, 0.5f * b2) / fmaf(fnu, a, 1.0f);
+  return s + fma(nu, double(corr), nu);
+}
+
 // The FP64 solve of the binned kernels: guess plus `steps` step64 steps; the
 // last step's Mills ratios are left in `last` for adjoint_reuse.
 __device__ __forceinline__ double solve64(int region, const Node<double>& nd, double lnbeta, int steps, Last& last) {
@@ -595,14 +660,13 @@ __device__ __forceinline__ double solve64(int region, const Node<double>& nd, do
 // steps, then one step64 with float derivative ratios from the float iterate
 // (x, bmax, bb and lnbeta in double).
 __device__ __forceinline__ double solve_mixed64(int region, const Node<float>& nf, double x, double bmax, double bb,
-                                                double lnbeta, int steps, Last& last) {
+                                                int steps, Last& last) {
+  const float lnbeta_f = (region == kLower) ? logf(nf.bb) : 0.0f; // beta >= 1e-30 on this path
   const float lnbetac_f = (region == kUpper) ? logf(nf.bb) : 0.0f;
-  const float inv_lnbeta_f = (region == kLower) ? 1.0f / float(lnbeta) : 0.0f;
-  float sf = region_guess<float>(region, nf, float(lnbeta));
+  const float inv_lnbeta_f = (region == kLower) ? 1.0f / lnbeta_f : 0.0f;
+  float sf = region_guess<float>(region, nf, lnbeta_f);
   for (int i = 1; i < steps; ++i) sf = householder_step<float>(nf.x, nf.bb, lnbetac_f, inv_lnbeta_f, region, sf);
-  const double lnbetac = (region == kUpper) ? log(bb) : 0.0;
-  const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
-  return step64<true>(x, bmax, bb, lnbetac, inv_lnbeta, region, double(sf), last);
+  return step64_final(x, bmax, bb, region, double(sf), sf, nf.x, last);
 }
 
 // Mixed precision (PIVOT_MODE_MIXED): the float node seeds a float guess and
@@ -738,7 +802,15 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   const double ya = near ? mills_shift(last.ya, last.za, za - last.za) : mills_small(za);
   const double yb = near ? mills_shift(last.yb, last.zb, zb - last.zb) : mills_small(zb);
   const double lbs = log_bs<double>(h, t);
-  double ibs = exp(-lbs), E1 = bmax * ibs, E2 = ibs / bmax;
+  double ibs;
+  if (last.ibs > 0.0 && fabs(lbs - last.lbs) < 1e-3) {
+    // 1/b_s from the last step's: exp(-d) to third order, d = lbs - last.lbs (|d| < 1e-3: d^4/24 < 5e-14)
+    const double d = lbs - last.lbs;
+    ibs = last.ibs * fma(fma(fma(d, -1.0 / 6.0, 0.5), d, -1.0), d, 1.0);
+  } else {
+    ibs = exp(-lbs);
+  }
+  double E1 = bmax * ibs, E2 = ibs / bmax;
   if (!finite64(ibs)) {
     // b_s underflows (|ln(F/K)| beyond ~1400): the reflections from their own exponents
     E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
