@@ -19,18 +19,7 @@ namespace M = pivot::mlp;
 
 constexpr int kLBlock = 128; // 4 warps
 constexpr int kLWarps = kLBlock / 32;
-constexpr int kLTile = 512;
-constexpr int kLRowsPerThread = kLTile / kLBlock;
 constexpr double kDefaultFallback = 1e-2;
-
-struct LearnedSmem {
-  M::Weights W;
-  __nv_bfloat16 tiles[kLWarps][2][M::kRows * M::LDA];
-  double x[kLTile], bmax[kLTile], bb[kLTile], lnb[kLTile], s0[kLTile];
-  uint16_t list[kLTile], order[kLTile], pos[kLTile];
-  uint8_t bin[kLTile];
-  int nsolve, cnt[3], off[4];
-};
 
 // The quote's normalised problem and its MLP features (lane = row); `has`
 // false gives neutral features for the lanes that only keep the warp full.
@@ -51,23 +40,77 @@ __device__ __forceinline__ LearnedRow learned_row(double F, double K, double T, 
   return r;
 }
 
+// ---------------------------------------------------------------------------
+// Inference (PIVOT_MODE_LEARNED), one 1,024-row tile per block of 256 threads:
+//  phase 1: rows that need no solve are finished (as in the binned kernel),
+//           the others listed; their time value and complement kept.
+//  phase 2: warps take the list 32 rows at a time: FP64 normalisation, the
+//           MLP seed s0 (features and baseline in float, network on tensor
+//           cores with activations in registers), and the row's objective:
+//           lower below the inflection b_c, middle up to beta = b_max/2,
+//           upper beyond.  Rows outside the float range (beta or beta_c below
+//           1e-30, |x| > 80) go straight to the fallback list.
+//  phase 3: rows objective after objective: `steps - 1` float Householder(3)
+//           steps from s0, then the FP64 final step of the mixed form, the
+//           gated adjoint.  A row is accepted when the float steps moved s0
+//           by at most `fallback` (relative) and the FP64 step moved the
+//           float iterate by at most 1e-5 -- its quartic error is then far
+//           below double rounding; otherwise it joins the fallback list.
+//  phase 4: the fallback rows, densely: LBR's rational seed and FP64 steps.
+// ---------------------------------------------------------------------------
+constexpr int kIBlock = 256;
+constexpr int kIWarps = kIBlock / 32;
+constexpr int kITile = 1024;
+constexpr int kIRowsPerThread = kITile / kIBlock;
+constexpr double kAcceptFinal = 1e-5;
+constexpr uint8_t kNoBin = 255;
+
+struct InferSmem {
+  M::Weights W;
+  double x[kITile], bmax[kITile], bb[kITile];
+  float s0[kITile];
+  uint16_t list[kITile], order[kITile], pos[kITile], fb[kITile];
+  uint8_t bin[kITile];
+  int nsolve, nfb, cnt[3], off[4];
+};
+
 template <bool kBackward>
-__global__ void __launch_bounds__(kLBlock, 2) k_iv_learned(Args a, const pivot_mlp* net, double fallback) {
+__device__ __forceinline__ void finish_row(const Args& a, int64_t i, double F, double K, double T, int fl, double s,
+                                           double x, double bmax, const pivot::Last& last) {
+  const double inv_sqT = rsqrt(T);
+  const double sig = s * inv_sqT;
+  a.sigma[i] = sig;
+  if (a.status) a.status[i] = 0;
+  if (kBackward) {
+    const double g = a.gbar ? a.gbar[i] : 1.0;
+    const pivot::Grad d = isnan(g) ? pivot::degenerate_grad(true, g, a.mode)
+                                   : pivot::adjoint_reuse(F, K, fl, sig, s, x, bmax, inv_sqT, rsqrt(F * K), g,
+                                                          a.tau, a.mode, last);
+    if (a.dP) a.dP[i] = d.dP;
+    if (a.dF) a.dF[i] = d.dF;
+    if (a.dK) a.dK[i] = d.dK;
+    if (a.dT) a.dT[i] = d.dT;
+  }
+}
+
+template <bool kBackward>
+__global__ void __launch_bounds__(kIBlock, 3) k_iv_learned(Args a, const pivot_mlp* net, double fallback) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  LearnedSmem& S = *reinterpret_cast<LearnedSmem*>(smem_raw);
+  InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   M::stage_weights(net, S.W, nullptr);
-  __syncthreads();
-  for (int64_t base = int64_t(blockIdx.x) * kLTile; base < a.n; base += int64_t(gridDim.x) * kLTile) {
+  const int fsteps = a.steps - 1; // float steps before the FP64 one
+  for (int64_t base = int64_t(blockIdx.x) * kITile; base < a.n; base += int64_t(gridDim.x) * kITile) {
     if (tid == 0) {
       S.nsolve = 0;
+      S.nfb = 0;
       S.cnt[0] = S.cnt[1] = S.cnt[2] = 0;
     }
     __syncthreads();
-    // ---- phase 1: finish rows that need no solve, list the others
+    // ---- phase 1
 #pragma unroll
-    for (int j = 0; j < kLRowsPerThread; ++j) {
-      const int r = j * kLBlock + tid;
+    for (int j = 0; j < kIRowsPerThread; ++j) {
+      const int r = j * kIBlock + tid;
       const int64_t i = base + r;
       bool solve = false;
       if (i < a.n) {
@@ -80,39 +123,53 @@ __global__ void __launch_bounds__(kLBlock, 2) k_iv_learned(Args a, const pivot_m
           if (kBackward) write_grad(a, i, F, K, T, fl, q.sigma);
         } else {
           solve = true;
+          S.bb[r] = q.tv;
+          S.x[r] = q.cv;
         }
       }
       const int slot = warp_append(solve, &S.nsolve, lane);
       if (solve) S.list[slot] = uint16_t(r);
     }
     __syncthreads();
-    // ---- phase 2: MLP seed for the listed rows, 32 per warp; the row's LBR objective:
-    //      lower below the inflection b_c, middle above it while beta <= b_max/2, upper beyond
+    // ---- phase 2: normalisation, MLP seed, objective
     const int nsolve = S.nsolve;
-    for (int c = warp; c * 32 < nsolve; c += kLWarps) {
+    for (int c = warp; c * 32 < nsolve; c += kIWarps) {
       const int qi = c * 32 + lane;
       const bool has = qi < nsolve;
       const int r = has ? S.list[qi] : 0;
-      LearnedRow row;
-      float f0 = 0.0f, f1 = 0.5f;
+      bool learned = false;
+      float f0 = 0.0f, f1 = 0.5f, bf = 0.0f;
+      double x = 0.0, bmax = 0.0, beta = 0.0, betac = 0.0;
       if (has) {
         const int64_t i = base + r;
-        row = learned_row(a.F[i], a.K[i], a.T[i], a.P[i], a.flag[i]);
-        f0 = row.f.f0;
-        f1 = row.f.f1;
+        const double F = a.F[i], K = a.K[i];
+        pivot::moneyness(F, K, x, bmax);
+        const double rsq = rsqrt(F * K);
+        beta = S.bb[r] * rsq;
+        betac = S.x[r] * rsq;
+        learned = beta > 1e-30 && betac > 1e-30 && x > -80.0;
+        if (learned) {
+          bf = float(beta);
+          f0 = float(-x);
+          f1 = rsqrtf(-2.0f * logf(bf));
+        }
       }
-      const float o = M::forward_warp(f0, f1, S.W, S.tiles[warp][0], S.tiles[warp][1]);
+      const float o = M::forward_regs(f0, f1, S.W); // every lane of the warp takes part
       int bin = -1;
       if (has) {
-        const double e = pivot::erfcx_fp64(sqrt(-row.x));
-        const bool low = row.beta <= 0.5 * row.bmax * (1.0 - e);
-        bin = low ? 0 : (row.beta <= row.betac ? 1 : 2);
-        S.x[r] = row.x;
-        S.bmax[r] = row.bmax;
-        S.bb[r] = (bin == 2) ? row.betac : row.beta;
-        S.lnb[r] = row.lnb;
-        S.s0[r] = row.f.sa * exp(double(o));
-        S.bin[r] = uint8_t(bin);
+        S.x[r] = x;
+        S.bmax[r] = bmax;
+        if (learned) {
+          const float s0 = fmaf(f0, f1, M::kSqrt2PiF * bf) * __expf(o);
+          const float e = erfcxf(sqrtf(f0));
+          const bool low = bf <= 0.5f * float(bmax) * (1.0f - e);
+          bin = low ? 0 : (beta <= betac ? 1 : 2);
+          if (!(s0 > 0.0f && s0 < INFINITY)) bin = -1;
+          S.s0[r] = s0;
+          S.bb[r] = (bin == 2) ? betac : beta;
+        }
+        if (bin < 0) S.fb[atomicAdd(&S.nfb, 1)] = uint16_t(r);
+        S.bin[r] = bin < 0 ? kNoBin : uint8_t(bin);
       }
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -128,58 +185,58 @@ __global__ void __launch_bounds__(kLBlock, 2) k_iv_learned(Args a, const pivot_m
       S.off[3] = S.off[2] + S.cnt[2];
     }
     __syncthreads();
-    for (int qi = tid; qi < nsolve; qi += kLBlock) {
+    for (int qi = tid; qi < nsolve; qi += kIBlock) {
       const int r = S.list[qi];
-      S.order[S.off[S.bin[r]] + S.pos[r]] = uint16_t(r);
+      const int b = S.bin[r];
+      if (b != kNoBin) S.order[S.off[b] + S.pos[r]] = uint16_t(r);
     }
     __syncthreads();
-    // ---- phase 3: FP64 Householder steps from the seed, objective after objective
+    // ---- phase 3: float steps from the seed, the FP64 final step, accept or defer
     const int total = S.off[3];
-    for (int qi = tid; qi < total; qi += kLBlock) {
+    for (int qi = tid; qi < total; qi += kIBlock) {
       const int r = S.order[qi];
       const int bn = (qi >= S.off[2]) ? 2 : (qi >= S.off[1]) ? 1 : 0;
-      const bool up = bn == 2;
       const int rg = bn == 0 ? pivot::kLower : bn == 1 ? pivot::kMidHigh : pivot::kUpper;
-      const int64_t i = base + r;
-      const double F = a.F[i], K = a.K[i], T = a.T[i];
-      const int fl = a.flag[i];
-      const double x = S.x[r], bb = S.bb[r];
-      const double lnbetac = up ? log(bb) : 0.0;
-      const double inv_lnbeta = (bn == 0) ? 1.0 / S.lnb[r] : 0.0;
-      double s = S.s0[r];
-      bool ok = s > 0.0 && s < INFINITY;
+      const double x = S.x[r], bb = S.bb[r], bmax = S.bmax[r];
+      const float xf = float(x), bbf = float(bb);
+      const float lnb = (rg == pivot::kMidHigh) ? 0.0f : logf(bbf);
+      const float lnbetac = (rg == pivot::kUpper) ? lnb : 0.0f;
+      const float inv_lnbeta = (rg == pivot::kLower) ? 1.0f / lnb : 0.0f;
+      const float s0 = S.s0[r];
+      float sf = s0;
+      for (int k = 0; k < fsteps; ++k) sf = pivot::householder_step<float>(xf, bbf, lnbetac, inv_lnbeta, rg, sf);
+      bool ok = sf > 0.0f && sf < INFINITY && fabsf(sf - s0) <= float(fallback) * sf;
+      pivot::Last last;
+      double s = 0.0;
       if (ok) {
-        const double s1 = pivot::householder_step<double>(x, bb, lnbetac, inv_lnbeta, rg, s);
-        ok = s1 > 0.0 && s1 < INFINITY && fabs(s1 - s) <= fallback * s1;
-        s = s1;
-        for (int k = 1; ok && k < a.steps; ++k) s = pivot::householder_step<double>(x, bb, lnbetac, inv_lnbeta, rg, s);
+        s = pivot::step64_final(x, bmax, bb, rg, double(sf), sf, xf, last);
+        ok = fabs(s - double(sf)) <= kAcceptFinal * s;
       }
-      if (!ok) {
-        // the seed is outside its trust region: LBR's rational guess and the FP64 path
-        const pivot::Quote q = pivot::classify_quote(F, K, T, a.P[i], fl);
-        double x2, bmax2;
-        pivot::moneyness(F, K, x2, bmax2);
-        const double rsq = rsqrt(F * K);
-        pivot::Node<double> nd;
-        const int rg2 = pivot::classify<double>(x2, bmax2, q.tv * rsq, q.cv * rsq, nd);
-        const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, a.P[i], fl) : 0.0;
-        s = pivot::solve_region<double>(rg2, nd, lnb2, a.steps);
+      if (ok) {
+        const int64_t i = base + r;
+        finish_row<kBackward>(a, i, a.F[i], a.K[i], a.T[i], a.flag[i], s, x, bmax, last);
+      } else {
+        S.fb[atomicAdd(&S.nfb, 1)] = uint16_t(r);
       }
-      const double inv_sqT = rsqrt(T);
-      const double sig = s * inv_sqT;
-      a.sigma[i] = sig;
-      if (a.status) a.status[i] = 0;
-      if (kBackward) {
-        const double g = a.gbar ? a.gbar[i] : 1.0;
-        const double xs = (F >= K) ? -x : x;
-        const pivot::Grad d = isnan(g) ? pivot::degenerate_grad(true, g, a.mode)
-                                       : pivot::adjoint_core(F, K, fl, sig, s, xs, inv_sqT, rsqrt(F * K), g,
-                                                             a.tau, a.mode);
-        if (a.dP) a.dP[i] = d.dP;
-        if (a.dF) a.dF[i] = d.dF;
-        if (a.dK) a.dK[i] = d.dK;
-        if (a.dT) a.dT[i] = d.dT;
-      }
+    }
+    __syncthreads();
+    // ---- phase 4: fallback rows on LBR's rational seed, FP64 steps
+    const int nfb = S.nfb;
+    for (int qi = tid; qi < nfb; qi += kIBlock) {
+      const int r = S.fb[qi];
+      const int64_t i = base + r;
+      const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
+      const int fl = a.flag[i];
+      const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
+      double x, bmax;
+      pivot::moneyness(F, K, x, bmax);
+      const double rsq = rsqrt(F * K);
+      pivot::Node<double> nd;
+      const int rg = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
+      const double lnb = (rg == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, P, fl) : 0.0;
+      pivot::Last last;
+      const double s = pivot::solve64(rg, nd, lnb, a.steps, last);
+      finish_row<kBackward>(a, i, F, K, T, fl, s, x, bmax, last);
     }
     __syncthreads();
   }
@@ -215,12 +272,9 @@ __global__ void __launch_bounds__(kLBlock) k_guess_mlp(int64_t n, const double* 
                                                        const pivot_mlp* net, double* __restrict__ s_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   M::Weights& W = *reinterpret_cast<M::Weights*>(smem_raw);
-  __nv_bfloat16* tiles = reinterpret_cast<__nv_bfloat16*>(smem_raw + ((sizeof(M::Weights) + 15) / 16) * 16);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   M::stage_weights(net, W, nullptr);
   __syncthreads();
-  __nv_bfloat16* RA = tiles + warp * 2 * M::kRows * M::LDA;
-  __nv_bfloat16* RB = RA + M::kRows * M::LDA;
   for (int64_t c0 = (int64_t(blockIdx.x) * kLWarps + warp) * 32; c0 < n; c0 += int64_t(gridDim.x) * kLWarps * 32) {
     const int64_t i = c0 + lane;
     bool has = false;
@@ -235,7 +289,7 @@ __global__ void __launch_bounds__(kLBlock) k_guess_mlp(int64_t n, const double* 
         f1 = row.f.f1;
       }
     }
-    const float o = M::forward_warp(f0, f1, W, RA, RB);
+    const float o = M::forward_regs(f0, f1, W);
     if (i < n) s_out[i] = has ? row.f.sa * exp(double(o)) : __longlong_as_double(0x7ff8000000000000LL);
   }
 }
@@ -366,7 +420,7 @@ namespace pivot {
 namespace detail {
 
 int launch_learned(const Args& a, const pivot_mlp* mlp, double fallback, bool backward, void* stream) {
-  const size_t smem = sizeof(LearnedSmem);
+  const size_t smem = sizeof(InferSmem);
   static thread_local int configured_device = -1;
   static thread_local int grid_cap = 0;
   int dev = 0;
@@ -375,19 +429,19 @@ int launch_learned(const Args& a, const pivot_mlp* mlp, double fallback, bool ba
     cudaFuncSetAttribute(k_iv_learned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     cudaFuncSetAttribute(k_iv_learned<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     int b0 = 0, b1 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_iv_learned<false>, kLBlock, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_iv_learned<true>, kLBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_iv_learned<false>, kIBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_iv_learned<true>, kIBlock, smem);
     const int b = (b0 < b1 ? b0 : b1) > 0 ? (b0 < b1 ? b0 : b1) : 1;
     grid_cap = b * sm_count();
     configured_device = dev;
   }
-  const int64_t tiles = (a.n + kLTile - 1) / kLTile;
+  const int64_t tiles = (a.n + kITile - 1) / kITile;
   const unsigned grid = unsigned(tiles < grid_cap ? tiles : grid_cap);
   const double fb = fallback > 0.0 ? fallback : kDefaultFallback;
   if (backward)
-    k_iv_learned<true><<<grid, kLBlock, smem, static_cast<cudaStream_t>(stream)>>>(a, mlp, fb);
+    k_iv_learned<true><<<grid, kIBlock, smem, static_cast<cudaStream_t>(stream)>>>(a, mlp, fb);
   else
-    k_iv_learned<false><<<grid, kLBlock, smem, static_cast<cudaStream_t>(stream)>>>(a, mlp, fb);
+    k_iv_learned<false><<<grid, kIBlock, smem, static_cast<cudaStream_t>(stream)>>>(a, mlp, fb);
   return launch_status();
 }
 
@@ -419,7 +473,7 @@ int pivot_iv_guess(int64_t n, const double* F, const double* K, const double* T,
     k_guess_rational<<<grid_for(n), kBlock, 0, st>>>(n, F, K, T, P, flag, s_out);
     return launch_status();
   }
-  const size_t smem = ((sizeof(M::Weights) + 15) / 16) * 16 + size_t(kLWarps) * 2 * M::kRows * M::LDA * 2;
+  const size_t smem = sizeof(M::Weights);
   cudaFuncSetAttribute(k_guess_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const int64_t chunks = (n + 32 * kLWarps - 1) / (32 * kLWarps);
   const int64_t cap = int64_t(4) * sm_count();

@@ -148,30 +148,92 @@ __device__ __forceinline__ Features features(double x, double beta, double lnbet
   return f;
 }
 
-// Forward pass of the 32 rows of a warp; lane r holds row r's features and
-// receives its output.  RA, RB: two [32][LDA] bf16 scratch tiles of the warp.
-__device__ __forceinline__ float forward_warp(float f0, float f1, const Weights& W, __nv_bfloat16* RA,
-                                              __nv_bfloat16* RB) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll 4
-  for (int j = 0; j < H; j += 2) {
-    const float z0 = fmaf(W.w1[2 * j], f0, fmaf(W.w1[2 * j + 1], f1, W.b1[j]));
-    const float z1 = fmaf(W.w1[2 * j + 2], f0, fmaf(W.w1[2 * j + 3], f1, W.b1[j + 1]));
-    const __nv_bfloat162 v = __floats2bfloat162_rn(silu(z0), silu(z1));
-    *reinterpret_cast<__nv_bfloat162*>(RA + lane * LDA + j) = v;
+// Forward pass of the 32 rows of a warp with every activation in registers:
+// the FP32 accumulator fragment of one m16n8k16 layer is the BF16 A fragment
+// of the next (columns 2t, 2t+1 of n-tiles 2k and 2k+1 are k-tile k's
+// a0/a1 and a2/a3 in the same lane), so no shared-memory tile is needed.
+// Layer 1 (2 -> 64) is evaluated in FP32 directly in that layout, layer 4
+// (64 -> 1) as a dot product reduced over the four lanes of a quad.  Same
+// arithmetic as the forward half of train_warp up to the summation order of
+// layer 4.
+// Lane r holds row r's features and receives its output.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ float forward_regs(float f0, float f1, const Weights& W) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+  float out = 0.0f;
+#pragma unroll 1
+  for (int mt = 0; mt < 2; ++mt) {
+    const int r0 = mt * 16 + g, r1 = r0 + 8;
+    const float x00 = __shfl_sync(0xffffffffu, f0, r0), x01 = __shfl_sync(0xffffffffu, f1, r0);
+    const float x10 = __shfl_sync(0xffffffffu, f0, r1), x11 = __shfl_sync(0xffffffffu, f1, r1);
+    // layer 1 straight into the A fragments of layer 2
+    uint32_t a[4][4];
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int c = ks * 16 + half * 8 + 2 * tq;
+        const float z00 = fmaf(W.w1[2 * c], x00, fmaf(W.w1[2 * c + 1], x01, W.b1[c]));
+        const float z01 = fmaf(W.w1[2 * c + 2], x00, fmaf(W.w1[2 * c + 3], x01, W.b1[c + 1]));
+        const float z10 = fmaf(W.w1[2 * c], x10, fmaf(W.w1[2 * c + 1], x11, W.b1[c]));
+        const float z11 = fmaf(W.w1[2 * c + 2], x10, fmaf(W.w1[2 * c + 3], x11, W.b1[c + 1]));
+        a[ks][2 * half] = pack_bf16(silu(z00), silu(z01));
+        a[ks][2 * half + 1] = pack_bf16(silu(z10), silu(z11));
+      }
+    }
+    // layers 2 and 3
+#pragma unroll
+    for (int layer = 0; layer < 2; ++layer) {
+      const __nv_bfloat16* Bt = layer == 0 ? W.w2t : W.w3t;
+      const float* bias = layer == 0 ? W.b2 : W.b3;
+      float c[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const __nv_bfloat16* Br = Bt + (nt * 8 + g) * LDW + ks * 16 + 2 * tq;
+          mma_16816(c[nt], a[ks], ld32(Br), ld32(Br + 8));
+        }
+      }
+      if (layer == 0) {
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+          const int col = nt * 8 + 2 * tq;
+          const int slot = (nt & 1) * 2;
+          a[nt >> 1][slot] = pack_bf16(silu(c[nt][0] + bias[col]), silu(c[nt][1] + bias[col + 1]));
+          a[nt >> 1][slot + 1] = pack_bf16(silu(c[nt][2] + bias[col]), silu(c[nt][3] + bias[col + 1]));
+        }
+      } else {
+        // layer 4 on the BF16-rounded activations of layer 3
+        float o0 = 0.0f, o1 = 0.0f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+          const int col = nt * 8 + 2 * tq;
+          const float w0 = W.w4[col], w1 = W.w4[col + 1];
+          o0 = fmaf(w0, __bfloat162float(__float2bfloat16_rn(silu(c[nt][0] + bias[col]))), o0);
+          o0 = fmaf(w1, __bfloat162float(__float2bfloat16_rn(silu(c[nt][1] + bias[col + 1]))), o0);
+          o1 = fmaf(w0, __bfloat162float(__float2bfloat16_rn(silu(c[nt][2] + bias[col]))), o1);
+          o1 = fmaf(w1, __bfloat162float(__float2bfloat16_rn(silu(c[nt][3] + bias[col + 1]))), o1);
+        }
+        o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
+        o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+        o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+        o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+        // rows r0 (quad g) and r1 back to lane = row
+        const int src = 4 * (lane & 7);
+        const float v0 = __shfl_sync(0xffffffffu, o0, src);
+        const float v1 = __shfl_sync(0xffffffffu, o1, src);
+        const int within = lane - mt * 16;
+        if (within >= 0 && within < 16) out = W.b4 + (within < 8 ? v0 : v1);
+      }
+    }
   }
-  __syncwarp();
-  warp_gemm<2, 8, 4>(RA, LDA, W.w2t, LDW,
-                     [&](int r, int c, float v) { RB[r * LDA + c] = __float2bfloat16_rn(silu(v + W.b2[c])); });
-  __syncwarp();
-  warp_gemm<2, 8, 4>(RB, LDA, W.w3t, LDW,
-                     [&](int r, int c, float v) { RA[r * LDA + c] = __float2bfloat16_rn(silu(v + W.b3[c])); });
-  __syncwarp();
-  float o = W.b4;
-#pragma unroll 8
-  for (int k = 0; k < H; ++k) o = fmaf(W.w4[k], __bfloat162float(RA[lane * LDA + k]), o);
-  __syncwarp();
-  return o;
+  return out;
 }
 
 // Per-warp scratch of the training pass.
