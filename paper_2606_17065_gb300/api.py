@@ -73,6 +73,76 @@ def _host_result(inputs, outs):
     return res
 
 
+# Host inputs of more than this many rows are streamed through the device in
+# chunks of this size on two CUDA streams, so that the copies of one chunk
+# overlap the kernels of the other.
+HOST_CHUNK = 1 << 21
+_streams = {}
+
+
+def _copy_streams(device):
+    key = device.index
+    if key not in _streams:
+        _streams[key] = (torch.cuda.Stream(device), torch.cuda.Stream(device))
+    return _streams[key]
+
+
+def _is_host(inputs):
+    return all((not isinstance(t, torch.Tensor)) or not t.is_cuda for t in inputs if t is not None)
+
+
+def _host_tensor(t, dtype):
+    if t is None:
+        return None
+    t = torch.as_tensor(t)
+    if t.dtype != dtype:
+        t = t.to(dtype)
+    return t.contiguous()
+
+
+def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args):
+    """Run one row-wise entry point.  `build_args(m, ins, outs)` returns its
+    arguments for m rows of device tensors, stream excluded.  Device inputs
+    run in place on the current stream; host inputs larger than HOST_CHUNK are
+    pipelined chunk by chunk (host -> device, kernel, device -> host on
+    alternating streams) into pinned host outputs."""
+    n = next(t for t in inputs if t is not None)
+    n = n.numel() if isinstance(n, torch.Tensor) else len(n)
+    if not _is_host(inputs) or n <= HOST_CHUNK:
+        dev = _device_of(*inputs)
+        ins = [_on(t, dev, d) for t, d in zip(inputs, in_dtypes)]
+        _check_lengths(n, *ins)
+        outs = [torch.empty(n, dtype=d, device=dev) for d in out_dtypes]
+        _native.call(name, *build_args(n, ins, outs), _stream(dev))
+        return _host_result(inputs, outs)
+    dev = _device_of()
+    hins = [_host_tensor(t, d) for t, d in zip(inputs, in_dtypes)]
+    _check_lengths(n, *hins)
+    houts = [torch.empty(n, dtype=d, pin_memory=True) for d in out_dtypes]
+    streams = _copy_streams(dev)
+    bufs = [([None if h is None else torch.empty(HOST_CHUNK, dtype=h.dtype, device=dev) for h in hins],
+             [torch.empty(HOST_CHUNK, dtype=d, device=dev) for d in out_dtypes]) for _ in streams]
+    main = torch.cuda.current_stream(dev)
+    for st in streams:
+        st.wait_stream(main)
+    for k, lo in enumerate(range(0, n, HOST_CHUNK)):
+        m = min(HOST_CHUNK, n - lo)
+        st = streams[k % 2]
+        dins, douts = bufs[k % 2]
+        with torch.cuda.stream(st):
+            ins = [None if h is None else d[:m] for d, h in zip(dins, hins)]
+            for d, h in zip(ins, hins):
+                if h is not None:
+                    d.copy_(h[lo:lo + m], non_blocking=True)
+            outs = [d[:m] for d in douts]
+            _native.call(name, *build_args(m, ins, outs), ctypes.c_void_p(st.cuda_stream))
+            for h, d in zip(houts, outs):
+                h[lo:lo + m].copy_(d, non_blocking=True)
+    for st in streams:
+        st.synchronize()
+    return houts
+
+
 def _check_lengths(n, *ts):
     for t in ts:
         if t is not None and t.numel() != n:
@@ -184,17 +254,13 @@ def iv_guess(F, K, T, P, flag, *, mode="fp64", mlp=None):
 def iv(F, K, T, P, flag, *, mode="fp64", householder: int = 0, status: bool = True, mlp=None,
        fallback: float = 0.0):
     """Implied volatility (Algorithm 1 forward); returns (sigma, status or None)."""
-    dev = _device_of(F, K, T, P, flag)
-    f, k, t, p = (_on(a, dev, torch.float64) for a in (F, K, T, P))
-    fl = _on(flag, dev, torch.int8)
-    n = f.numel()
-    _check_lengths(n, k, t, p, fl)
-    sig = torch.empty(n, dtype=torch.float64, device=dev)
-    st = torch.empty(n, dtype=torch.uint8, device=dev) if status else None
     o = _opts(mode, householder, mlp, fallback)
-    _native.call("pivot_iv_forward", n, _p(f), _p(k), _p(t), _p(p), _p(fl), _p(sig), _p(st), ctypes.byref(o),
-                 _stream(dev))
-    return tuple(_host_result((F, K, T, P, flag), [sig, st]))
+    f64 = torch.float64
+    outs = _rows_call("pivot_iv_forward", (F, K, T, P, flag), (f64, f64, f64, f64, torch.int8),
+                      (f64, torch.uint8) if status else (f64,),
+                      lambda m, i, u: (m, *[_p(t) for t in i], _p(u[0]), _p(u[1]) if status else None,
+                                       ctypes.byref(o)))
+    return (outs[0], outs[1] if status else None)
 
 
 def iv_backward(F, K, T, flag, sigma, gbar=None, *, tau: float = 1e-6, gate="nan"):
@@ -214,19 +280,14 @@ def iv_backward(F, K, T, flag, sigma, gbar=None, *, tau: float = 1e-6, gate="nan
 def iv_forward_backward(F, K, T, P, flag, gbar=None, *, tau: float = 1e-6, gate="nan", mode="fp64",
                         householder: int = 0, mlp=None, fallback: float = 0.0):
     """Forward and gated adjoint in one pass; returns (sigma, status, dP, dF, dK, dT)."""
-    dev = _device_of(F, K, T, P, flag, gbar)
-    f, k, t, p = (_on(a, dev, torch.float64) for a in (F, K, T, P))
-    fl = _on(flag, dev, torch.int8)
-    g = _on(gbar, dev, torch.float64)
-    n = f.numel()
-    _check_lengths(n, k, t, p, fl, g)
-    sig = torch.empty(n, dtype=torch.float64, device=dev)
-    st = torch.empty(n, dtype=torch.uint8, device=dev)
-    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
     o = _opts(mode, householder, mlp, fallback)
-    _native.call("pivot_iv_forward_backward", n, _p(f), _p(k), _p(t), _p(p), _p(fl), _p(g), float(tau),
-                 _gate(gate), _p(sig), _p(st), *[_p(x) for x in outs], ctypes.byref(o), _stream(dev))
-    return tuple(_host_result((F, K, T, P, flag, gbar), [sig, st, *outs]))
+    f64 = torch.float64
+    gm = _gate(gate)
+    outs = _rows_call("pivot_iv_forward_backward", (F, K, T, P, flag, gbar),
+                      (f64, f64, f64, f64, torch.int8, f64), (f64, torch.uint8, f64, f64, f64, f64),
+                      lambda m, i, u: (m, *[_p(t) for t in i], float(tau), gm, *[_p(t) for t in u],
+                                       ctypes.byref(o)))
+    return tuple(outs)
 
 
 class ImpliedVol(torch.autograd.Function):
@@ -306,17 +367,13 @@ def bs_price(S, K, T, r, q, sigma, flag, *, vega: bool = True):
 
 def bs_iv(S, K, T, r, q, V, flag, *, mode="fp64", householder: int = 0, status: bool = True):
     """Implied volatility from the discounted price; returns (sigma, status or None)."""
-    dev = _device_of(S, K, T, r, q, V, flag)
-    s_, k, t, rr, qq, v = (_on(a, dev, torch.float64) for a in (S, K, T, r, q, V))
-    fl = _on(flag, dev, torch.int8)
-    n = s_.numel()
-    _check_lengths(n, k, t, rr, qq, v, fl)
-    sig = torch.empty(n, dtype=torch.float64, device=dev)
-    st = torch.empty(n, dtype=torch.uint8, device=dev) if status else None
     o = _opts(mode, householder)
-    _native.call("pivot_bs_iv_forward", n, _p(s_), _p(k), _p(t), _p(rr), _p(qq), _p(v), _p(fl), _p(sig), _p(st),
-                 ctypes.byref(o), _stream(dev))
-    return tuple(_host_result((S, K, T, r, q, V, flag), [sig, st]))
+    f64 = torch.float64
+    outs = _rows_call("pivot_bs_iv_forward", (S, K, T, r, q, V, flag), (f64,) * 6 + (torch.int8,),
+                      (f64, torch.uint8) if status else (f64,),
+                      lambda m, i, u: (m, *[_p(t) for t in i], _p(u[0]), _p(u[1]) if status else None,
+                                       ctypes.byref(o)))
+    return (outs[0], outs[1] if status else None)
 
 
 def bs_iv_backward(S, K, T, r, q, flag, sigma, gbar=None, *, tau: float = 1e-6, gate="nan"):
@@ -336,19 +393,14 @@ def bs_iv_backward(S, K, T, r, q, flag, sigma, gbar=None, *, tau: float = 1e-6, 
 def bs_iv_forward_backward(S, K, T, r, q, V, flag, gbar=None, *, tau: float = 1e-6, gate="nan", mode="fp64",
                            householder: int = 0):
     """Forward and gated adjoint in xi in one pass; returns (sigma, status, dV, dS, dK, dT, dr, dq)."""
-    dev = _device_of(S, K, T, r, q, V, flag, gbar)
-    s_, k, t, rr, qq, v = (_on(a, dev, torch.float64) for a in (S, K, T, r, q, V))
-    fl = _on(flag, dev, torch.int8)
-    g = _on(gbar, dev, torch.float64)
-    n = s_.numel()
-    _check_lengths(n, k, t, rr, qq, v, fl, g)
-    sig = torch.empty(n, dtype=torch.float64, device=dev)
-    st = torch.empty(n, dtype=torch.uint8, device=dev)
-    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(6)]
     o = _opts(mode, householder)
-    _native.call("pivot_bs_iv_forward_backward", n, _p(s_), _p(k), _p(t), _p(rr), _p(qq), _p(v), _p(fl), _p(g),
-                 float(tau), _gate(gate), _p(sig), _p(st), *[_p(x) for x in outs], ctypes.byref(o), _stream(dev))
-    return tuple(_host_result((S, K, T, r, q, V, flag, gbar), [sig, st, *outs]))
+    f64 = torch.float64
+    gm = _gate(gate)
+    outs = _rows_call("pivot_bs_iv_forward_backward", (S, K, T, r, q, V, flag, gbar),
+                      (f64,) * 6 + (torch.int8, f64), (f64, torch.uint8) + (f64,) * 6,
+                      lambda m, i, u: (m, *[_p(t) for t in i], float(tau), gm, *[_p(t) for t in u],
+                                       ctypes.byref(o)))
+    return tuple(outs)
 
 
 class ImpliedVolBS(torch.autograd.Function):
