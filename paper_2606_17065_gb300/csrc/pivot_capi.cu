@@ -129,12 +129,16 @@ struct TileCfg {
   // six node fields per row (+ e^{r tau}, e^{(r-q) tau} in the Black-Scholes form), two row lists
   static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
 };
-// mixed mode: 4 float-seeded region bins plus 4 FP64 bins for rows outside
-// the float range (beta or b_max - beta below kMixedFloor, or |x| above
-// kMixedMaxAbsX, where the float node would underflow)
-constexpr int kBins = 8;
+// Region bins: 4 in the FP64 form.  The mixed form has 4 float-seeded region
+// bins, 4 FP64 bins for rows outside the float range (b_max - beta below
+// kMixedFloor, |x| above kMixedMaxAbsX, or beta below kMixedFloor near the
+// money), and bin kDeepBin: lower-tail rows with beta below kMixedFloor and
+// |x| >= kDeepMinAbsX, seeded in float from ln beta (float_deep_seed).
+constexpr int kMaxBins = 9;
+constexpr int kDeepBin = 8;
 constexpr double kMixedFloor = 1e-30;
 constexpr double kMixedMaxAbsX = 80.0;
+constexpr double kDeepMinAbsX = 0.1;
 
 // Row inputs in forward coordinates.  The Black-Scholes form (kBS) reads the
 // spot S from a.F and the discounted price V from a.P and maps them with the
@@ -168,8 +172,9 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
   uint16_t* s_list = reinterpret_cast<uint16_t*>(s_ec + (kBS ? kTile : 0));  // phase 1 -> 2: rows to solve
   uint16_t* s_order = s_list + kTile;                                        // phase 2 -> 3: region order
   __shared__ int s_nsolve;
-  __shared__ int s_cnt[kBins];
-  __shared__ int s_off[kBins + 1];
+  constexpr int kBins = kMixed ? 9 : 4;
+  __shared__ int s_cnt[kMaxBins];
+  __shared__ int s_off[kMaxBins + 1];
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -231,7 +236,16 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
         const double rsq = rsqrt(F * K);
         const double beta = s_bb[r] * rsq, betac = s_e[r] * rsq;
         bool fp64_row = true;
-        if (kMixed && beta > kMixedFloor && betac > kMixedFloor && x > -kMixedMaxAbsX) {
+        if (kMixed && !(beta > kMixedFloor) && betac > kMixedFloor && x > -kMixedMaxAbsX && x <= -kDeepMinAbsX &&
+            pivot::pos_normal(beta)) {
+          // deep lower tail: beta below the float range but ln beta is not (at |x| >= 0.1 such a
+          // beta lies below b_l, in the lower region)
+          fp64_row = false;
+          rg = kDeepBin;
+          s_x[r] = x;
+          s_bmax[r] = bmax;
+          s_bb[r] = beta;
+        } else if (kMixed && beta > kMixedFloor && betac > kMixedFloor && x > -kMixedMaxAbsX) {
           // float node and region; the float copies are exact in double storage
           pivot::Node<float> nf;
           rg = pivot::classify<float>(float(x), float(bmax), float(beta), float(betac), nf);
@@ -289,14 +303,28 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
       double F, P;
       row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
       const int fl = a.flag[i];
-      const int rg = bin & 3;
+      const bool deep = kMixed && bin == kDeepBin;
+      const int rg = deep ? int(pivot::kLower) : (bin & 3);
+      const bool float_row = kMixed && (bin < 4 || deep);
       const double bb = s_bb[r];
       // ln beta for the FP64 solve of a lower-region row (the float-seeded rows of the mixed form do without)
-      const double lnbeta =
-          (rg == pivot::kLower && !(kMixed && bin < 4)) ? pivot::log_beta(bb, F, K, T, P, fl) : 0.0;
+      const double lnbeta = (rg == pivot::kLower && !float_row) ? pivot::log_beta(bb, F, K, T, P, fl) : 0.0;
       double s = 0.0;
       pivot::Last last;
-      if (kMixed && bin < 4) {
+      if (deep) {
+        s = pivot::solve_deep_mixed64(s_x[r], s_bmax[r], bb, last);
+        if (!(s > 0.0 && s < INFINITY)) {
+          // not accepted: the FP64 path from the row's inputs
+          const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
+          double x, bmax;
+          pivot::moneyness(F, K, x, bmax);
+          const double rsq = rsqrt(F * K);
+          pivot::Node<double> nd;
+          const int rg2 = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
+          const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, P, fl) : 0.0;
+          s = pivot::solve64(rg2, nd, lnb2, a.steps, last);
+        }
+      } else if (kMixed && bin < 4) {
         pivot::Node<float> nf;
         const float2 p0 = *reinterpret_cast<const float2*>(&s_e[r]);
         const float2 p1 = *reinterpret_cast<const float2*>(&s_bn[r]);

@@ -220,6 +220,10 @@ __device__ __forceinline__ bool pos_finite(double v) {
 __device__ __forceinline__ bool finite64(double v) {
   return (uint64_t(__double_as_longlong(v)) & 0x7fffffffffffffffull) < 0x7ff0000000000000ull;
 }
+// positive and normal (neither zero, subnormal, infinite nor NaN)
+__device__ __forceinline__ bool pos_normal(double v) {
+  return uint64_t(__double_as_longlong(v)) - 0x0010000000000000ull < 0x7fe0000000000000ull;
+}
 // v < 0 for a non-NaN v (-0 is not negative)
 __device__ __forceinline__ bool neg64(double v) {
   return uint64_t(__double_as_longlong(v)) > 0x8000000000000000ull;
@@ -667,6 +671,42 @@ __device__ __forceinline__ double solve_mixed64(int region, const Node<float>& n
   float sf = region_guess<float>(region, nf, lnbeta_f);
   for (int i = 1; i < steps; ++i) sf = householder_step<float>(nf.x, nf.bb, lnbetac_f, inv_lnbeta_f, region, sf);
   return step64_final(x, bmax, bb, region, double(sf), sf, nf.x, last);
+}
+
+// ln v in float for a positive normal double v of any exponent: v = m 2^e with
+// m in [1, 2) read off the bit pattern (its top 23 mantissa bits), so no value
+// leaves the float range.
+__device__ __forceinline__ float log_of_double_f(double v) {
+  const uint64_t b = uint64_t(__double_as_longlong(v));
+  const int e = int((b >> 52) & 0x7ff) - 1023;
+  const float m = __int_as_float(0x3f800000 | int((b >> 29) & 0x7fffff));
+  return fmaf(float(e), 0.693147180559945309f, logf(m));
+}
+
+constexpr double kDeepAccept = 1e-5;
+
+// The mixed solve of a deep lower-tail row (beta below the float range,
+// |x| >= 0.1).  Far in the lower tail b ~ b_s rho with rho ~ s^3/x^2 (the
+// Mills ratios' leading terms), i.e.
+//   ln beta ~ -x^2/(2 s^2) - s^2/8 + 3 ln s - 2 ln|x| - ln sqrt(2 pi),
+// whose solution for s by one fixed-point pass from s_a = |x|/sqrt(-2 ln beta)
+// seeds two float Householder(3) steps on the lower objective (which needs
+// only ln beta) and the final FP64 step.  Returns NaN when the FP64 step moves
+// the float iterate by more than kDeepAccept (relative): the caller then
+// takes the FP64 path.
+__device__ __forceinline__ double solve_deep_mixed64(double x, double bmax, double beta, Last& last) {
+  const float lnb = log_of_double_f(beta);
+  const float ax = float(-x), xf = -ax;
+  const float lax = logf(ax);
+  const float sa = ax * rsqrtf(-2.0f * lnb);
+  const float w = -lnb + 3.0f * logf(sa) - 2.0f * lax - float(kLnSqrt2Pi) - 0.125f * sa * sa;
+  float sf = w > 0.0f ? ax * rsqrtf(2.0f * w) : sa;
+  const float inv_lnb = 1.0f / lnb;
+  sf = householder_step<float>(xf, 0.0f, 0.0f, inv_lnb, kLower, sf);
+  sf = householder_step<float>(xf, 0.0f, 0.0f, inv_lnb, kLower, sf);
+  if (!(sf > 0.0f && sf < INFINITY)) return __longlong_as_double(0x7ff8000000000000LL);
+  const double s = step64_final(x, bmax, beta, kLower, double(sf), sf, xf, last);
+  return fabs(s - double(sf)) <= kDeepAccept * s ? s : __longlong_as_double(0x7ff8000000000000LL);
 }
 
 // Mixed precision (PIVOT_MODE_MIXED): the float node seeds a float guess and
