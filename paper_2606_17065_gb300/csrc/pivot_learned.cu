@@ -48,8 +48,11 @@ __device__ __forceinline__ LearnedRow learned_row(double F, double K, double T, 
 //           MLP seed s0 (features and baseline in float, network on tensor
 //           cores with activations in registers), and the row's objective:
 //           lower below the inflection b_c, middle up to beta = b_max/2,
-//           upper beyond.  Rows outside the float range (beta or beta_c below
-//           1e-30, |x| > 80) go straight to the fallback list.
+//           upper beyond.  Lower-tail rows whose beta is below the float
+//           range (|x| >= 0.1) take the float seed from ln beta of the mixed
+//           form instead (bin 3); other rows outside the float range (beta_c
+//           below 1e-30, |x| > 80, tiny beta near the money) go straight to
+//           the fallback list.
 //  phase 3: rows objective after objective: `steps - 1` float Householder(3)
 //           steps from s0, then the FP64 final step of the mixed form, the
 //           gated adjoint.  A row is accepted when the float steps moved s0
@@ -71,8 +74,11 @@ struct InferSmem {
   float s0[kITile];
   uint16_t list[kITile], order[kITile], pos[kITile], fb[kITile];
   uint8_t bin[kITile];
-  int nsolve, nfb, cnt[3], off[4];
+  int nsolve, nfb, cnt[4], off[5];
 };
+// bins 0-2: the MLP-seeded objectives; bin 3: deep lower-tail rows (beta below
+// the float range, |x| >= 0.1), seeded in float from ln beta as in the mixed form
+constexpr int kIBins = 4;
 
 template <bool kBackward>
 __device__ __forceinline__ void finish_row(const Args& a, int64_t i, double F, double K, double T, int fl, double s,
@@ -104,7 +110,7 @@ __global__ void __launch_bounds__(kIBlock, 3) k_iv_learned(Args a, const pivot_m
     if (tid == 0) {
       S.nsolve = 0;
       S.nfb = 0;
-      S.cnt[0] = S.cnt[1] = S.cnt[2] = 0;
+      S.cnt[0] = S.cnt[1] = S.cnt[2] = S.cnt[3] = 0;
     }
     __syncthreads();
     // ---- phase 1
@@ -159,6 +165,10 @@ __global__ void __launch_bounds__(kIBlock, 3) k_iv_learned(Args a, const pivot_m
       if (has) {
         S.x[r] = x;
         S.bmax[r] = bmax;
+        if (!learned && !(beta > 1e-30) && betac > 1e-30 && x <= -0.1 && x > -80.0 && pivot::pos_normal(beta)) {
+          bin = 3;
+          S.bb[r] = beta;
+        }
         if (learned) {
           const float s0 = fmaf(f0, f1, M::kSqrt2PiF * bf) * __expf(o);
           const float e = erfcxf(sqrtf(f0));
@@ -172,7 +182,7 @@ __global__ void __launch_bounds__(kIBlock, 3) k_iv_learned(Args a, const pivot_m
         S.bin[r] = bin < 0 ? kNoBin : uint8_t(bin);
       }
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < kIBins; ++k) {
         const int p = warp_append(bin == k, &S.cnt[k], lane);
         if (bin == k) S.pos[r] = uint16_t(p);
       }
@@ -180,9 +190,7 @@ __global__ void __launch_bounds__(kIBlock, 3) k_iv_learned(Args a, const pivot_m
     __syncthreads();
     if (tid == 0) {
       S.off[0] = 0;
-      S.off[1] = S.cnt[0];
-      S.off[2] = S.off[1] + S.cnt[1];
-      S.off[3] = S.off[2] + S.cnt[2];
+      for (int k = 0; k < kIBins; ++k) S.off[k + 1] = S.off[k] + S.cnt[k];
     }
     __syncthreads();
     for (int qi = tid; qi < nsolve; qi += kIBlock) {
@@ -192,9 +200,22 @@ __global__ void __launch_bounds__(kIBlock, 3) k_iv_learned(Args a, const pivot_m
     }
     __syncthreads();
     // ---- phase 3: float steps from the seed, the FP64 final step, accept or defer
-    const int total = S.off[3];
+    const int total = S.off[kIBins];
     for (int qi = tid; qi < total; qi += kIBlock) {
       const int r = S.order[qi];
+      if (qi >= S.off[3]) {
+        // deep lower tail
+        pivot::Last last;
+        const double x = S.x[r], bmax = S.bmax[r];
+        const double s = pivot::solve_deep_mixed64(x, bmax, S.bb[r], last);
+        if (s > 0.0 && s < INFINITY) {
+          const int64_t i = base + r;
+          finish_row<kBackward>(a, i, a.F[i], a.K[i], a.T[i], a.flag[i], s, x, bmax, last);
+        } else {
+          S.fb[atomicAdd(&S.nfb, 1)] = uint16_t(r);
+        }
+        continue;
+      }
       const int bn = (qi >= S.off[2]) ? 2 : (qi >= S.off[1]) ? 1 : 0;
       const int rg = bn == 0 ? pivot::kLower : bn == 1 ? pivot::kMidHigh : pivot::kUpper;
       const double x = S.x[r], bb = S.bb[r], bmax = S.bmax[r];
