@@ -254,7 +254,7 @@ def body_variants(dev, stream, steps):
 
     # the learned seed: trained first by the library's kernels on 16M operator-generated pairs
     from paper_2606_17065_gb300 import training
-    trainer, hist, train_s = training.train_learned_guess(n_rows=workloads.STRESS_N, steps=3000, batch=32768,
+    trainer, hist, train_s = training.train_learned_guess(n_rows=workloads.STRESS_N, steps=12000, batch=32768,
                                                           lr=3e-3, seed=4, device=dev)
 
     def run(mode):
@@ -270,7 +270,7 @@ def body_variants(dev, stream, steps):
     plain = time_variant(lambda: run(0), n, stream, steps)
     mixed = time_variant(lambda: run(1), n, stream, steps)
     learned = time_variant(lambda: run(2), n, stream, steps)
-    learned["training"] = {"pairs": workloads.STRESS_N, "adam_steps": 3000, "batch": 32768, "seconds": train_s,
+    learned["training"] = {"pairs": workloads.STRESS_N, "adam_steps": 12000, "batch": 32768, "seconds": train_s,
                            "final_mse_ln_s": hist[-1][1]}
     run(0)
     s64 = sig.clone()

@@ -101,10 +101,12 @@ typedef struct {
 
 typedef struct {
   int32_t mode;          /* PIVOT_MODE_* ; default PIVOT_MODE_FP64 */
-  int32_t householder;   /* Householder(3) iterations after the initial guess, 0 = default (2), max 4 */
+  int32_t householder;   /* Householder(3) iterations after the initial guess, 0 = default (2), max 4;
+                            MIXED and LEARNED: the last one in FP64, the others in float */
   const pivot_mlp* mlp;  /* PIVOT_MODE_LEARNED: device pointer to the weights, else ignored */
-  double fallback;       /* PIVOT_MODE_LEARNED: a first Householder correction |ds|/s above this sends
-                            the row to the rational-guess path; 0 = default 1e-2 */
+  double fallback;       /* PIVOT_MODE_LEARNED: float steps moving the MLP seed by more than this
+                            (relative), or a final FP64 step moving the float iterate by more than
+                            1e-5, send the row to the rational-guess FP64 path; 0 = default 0.25 */
 } pivot_opts;
 
 /*

@@ -19,7 +19,7 @@ namespace M = pivot::mlp;
 
 constexpr int kLBlock = 128; // 4 warps
 constexpr int kLWarps = kLBlock / 32;
-constexpr double kDefaultFallback = 1e-2;
+constexpr double kDefaultFallback = 0.25;
 
 // The quote's normalised problem and its MLP features (lane = row); `has`
 // false gives neutral features for the lanes that only keep the warp full.
@@ -41,7 +41,8 @@ __device__ __forceinline__ LearnedRow learned_row(double F, double K, double T, 
 }
 
 // ---------------------------------------------------------------------------
-// Inference (PIVOT_MODE_LEARNED), one 1,024-row tile per block of 256 threads:
+// Inference (PIVOT_MODE_LEARNED), one 2,048-row tile per block of 256 threads
+// (2 blocks per SM):
 //  phase 1: rows that need no solve are finished (as in the binned kernel),
 //           the others listed; their time value and complement kept.
 //  phase 2: warps take the list 32 rows at a time: FP64 normalisation, the
@@ -63,7 +64,7 @@ __device__ __forceinline__ LearnedRow learned_row(double F, double K, double T, 
 // ---------------------------------------------------------------------------
 constexpr int kIBlock = 256;
 constexpr int kIWarps = kIBlock / 32;
-constexpr int kITile = 1024;
+constexpr int kITile = 2048;
 constexpr int kIRowsPerThread = kITile / kIBlock;
 constexpr double kAcceptFinal = 1e-5;
 constexpr uint8_t kNoBin = 255;
@@ -100,7 +101,7 @@ __device__ __forceinline__ void finish_row(const Args& a, int64_t i, double F, d
 }
 
 template <bool kBackward>
-__global__ void __launch_bounds__(kIBlock, 3) k_iv_learned(Args a, const pivot_mlp* net, double fallback) {
+__global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_mlp* net, double fallback) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
