@@ -379,8 +379,10 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R u = (beta > M::kTiny) ? M::cbrt_(beta / kap) : M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
       const R ul = M::cbrt_(bl / kap);
       const R al = ax * R(kInvSqrt3) / sl;
-      const R Gl = M::ncdf_(-al);
-      const R dGl = R(3) * bl * (R(kInvSqrt2Pi) * M::exp_(R(-0.5) * al * al)) * al / (sl * ul * bsl);
+      // Phi(-al) = phi(al) Y(-al) = exp(-al^2/2) erfcx(al/sqrt 2) / 2: one exponential shared with phi(al)
+      const R eal = M::exp_(R(-0.5) * al * al);
+      const R Gl = R(0.5) * eal * M::erfcx_(al * R(kInvSqrt2));
+      const R dGl = R(3) * bl * (R(kInvSqrt2Pi) * eal) * al / (sl * ul * bsl);
       const R r = shape_monotone<R>(ul, R(0), Gl, R(1), dGl);
       const R G = M::fmin_(rational_cubic<R>(u, R(0), ul, R(0), Gl, R(1), dGl, r), R(0.5));
       return ax * R(kInvSqrt3) / (-M::ncdfinv_(G));
@@ -411,8 +413,10 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       // v = Phi(-s/2) against u = (b_max - beta)/2 on [0, u_u], v'(0) = 1.
       const R su = sc + R(kSqrtPiOver2) * (R(1) + e);
       const R uu = R(0.5) * nd.bn;
-      const R vu = M::ncdf_(R(-0.5) * su);
-      const R dvu = (R(kInvSqrt2Pi) * M::exp_(R(-0.125) * su * su)) / nd.bsn;
+      // Phi(-su/2) and phi(su/2) from one exponential, as in the lower region
+      const R esu = M::exp_(R(-0.125) * su * su);
+      const R vu = R(0.5) * esu * M::erfcx_(su * R(0.5 * kInvSqrt2));
+      const R dvu = (R(kInvSqrt2Pi) * esu) / nd.bsn;
       const R r = shape_monotone<R>(uu, R(0), vu, R(1), dvu);
       const R v = M::fmin_(rational_cubic<R>(R(0.5) * nd.bb, R(0), uu, R(0), vu, R(1), dvu, r), R(0.5));
       return R(-2) * M::ncdfinv_(v);
@@ -527,7 +531,7 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
     E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
     beta_ibs = exp(log(beta) - lbs);
   }
-  double nu, L = 0.0, q = 0.0;
+  double nu, L = 0.0, q = 0.0, iL = 0.0;
   if (region == kUpper) {
     const double gam = (hpt > 0.0) ? ya + yb : (E1 - ya) + yb;
     q = 1.0 / gam;
@@ -536,7 +540,10 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
     const double rho = taylor ? rho_taylor<double>(h, t) : (hpt <= 0.0 ? ya - yb : (E1 - ya) - yb);
     if (region == kLower) {
       L = lbs + log(rho); // ln b
-      q = 1.0 / rho;
+      // 1/rho and 1/L from one division: 1/rho = L / (rho L), 1/L = rho / (rho L)
+      const double inv = 1.0 / (rho * L);
+      q = L * inv;
+      iL = rho * inv;
       nu = rho * L * (1.0 - L * inv_lnbeta);
     } else {
       nu = beta_ibs - rho;
@@ -549,9 +556,9 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
     float h2 = b2, h3 = b3;
     const float fq = float(q);
     if (region == kLower) {
-      const float iL = 1.0f / float(L);
-      h2 = b2 - fq * fmaf(2.0f, iL, 1.0f);
-      h3 = b3 - 3.0f * b2 * fq + 2.0f * fq * fq - 6.0f * fq * (b2 - fq) * iL + 6.0f * fq * fq * iL * iL;
+      const float fiL = float(iL);
+      h2 = b2 - fq * fmaf(2.0f, fiL, 1.0f);
+      h3 = b3 - 3.0f * b2 * fq + 2.0f * fq * fq - 6.0f * fq * (b2 - fq) * fiL + 6.0f * fq * fq * fiL * fiL;
     } else if (region == kUpper) {
       h2 = b2 + fq;
       h3 = b3 + 3.0f * fq * b2 + 2.0f * fq * fq;
@@ -567,7 +574,6 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   const double b3 = fma(b2, b2, -3.0 * hh * inv_s * inv_s) - 0.25;
   double h2 = b2, h3 = b3;
   if (region == kLower) {
-    const double iL = 1.0 / L;
     h2 = b2 - q * fma(2.0, iL, 1.0);
     h3 = b3 - 3.0 * b2 * q + 2.0 * q * q - 6.0 * q * (b2 - q) * iL + 6.0 * q * q * iL * iL;
   } else if (region == kUpper) {
