@@ -130,6 +130,16 @@ __device__ __noinline__ R mills_y(R z) {
   return R(kSqrtPiOver2) * Math<R>::erfcx_(-z * R(kInvSqrt2));
 }
 
+// Y(z) for z <= 0: no reflection branch
+static __device__ __noinline__ double mills_small(double z) { return kSqrtPiOver2 * erfcx_nonneg(-z * kInvSqrt2); }
+// ... in either precision (the float path keeps mills_y)
+template <typename R>
+__device__ __forceinline__ R mills_nonpos(R z);
+template <>
+__device__ __forceinline__ double mills_nonpos<double>(double z) { return mills_small(z); }
+template <>
+__device__ __forceinline__ float mills_nonpos<float>(float z) { return mills_y<float>(z); }
+
 // ln b_s(x, s) = -(h^2 + t^2)/2 - ln sqrt(2 pi)
 template <typename R>
 __device__ __forceinline__ R log_bs(R h, R t) {
@@ -138,7 +148,7 @@ __device__ __forceinline__ R log_bs(R h, R t) {
 
 template <typename R>
 __device__ __forceinline__ R rho_taylor(R h, R t) {
-  R c_prev = mills_y<R>(h);                 // c_0
+  R c_prev = mills_nonpos<R>(h);            // c_0 (h <= 0)
   R c_cur = Math<R>::fma_(h, c_prev, R(1)); // c_1
   const R t2 = t * t;
   R acc = c_cur, tp = R(1);
@@ -343,8 +353,9 @@ __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& n
   const bool has_l = sl > R(0);
   const R sn = low ? (has_l ? sl : R(1)) : su;
   const R h = x / sn, t = R(0.5) * sn;
-  const R y1 = mills_y<R>(low ? h + t : -h - t);
-  const R y2 = mills_y<R>(h - t);
+  // both arguments are <= 0: h + t < 0 below s_c, -h - t < 0 above it, h - t < 0 always
+  const R y1 = mills_nonpos<R>(low ? h + t : -h - t);
+  const R y2 = mills_nonpos<R>(h - t);
   const R bs = M::exp_(log_bs<R>(h, t));
   const R val = bs * (low ? y1 - y2 : y1 + y2);
   nd.x = x;
@@ -499,8 +510,6 @@ struct Last {
   bool pair;     // false: the Taylor zone of rho evaluated neither
 };
 
-// Y(z) for z <= 0: no reflection branch
-static __device__ __noinline__ double mills_small(double z) { return kSqrtPiOver2 * erfcx_nonneg(-z * kInvSqrt2); }
 
 template <bool kF32Ratios>
 __device__ __forceinline__ double step64(double x, double bmax, double beta, double lnbetac, double inv_lnbeta,
@@ -585,15 +594,6 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   return s + num / den;
 }
 
-// Guess plus `steps` Householder(3) steps for a classified row; returns s.
-template <typename R>
-__device__ __forceinline__ R solve_region(int region, const Node<R>& nd, R lnbeta, int steps) {
-  const R lnbetac = (region == kUpper) ? Math<R>::log_(nd.bb) : R(0);
-  const R inv_lnbeta = (region == kLower) ? R(1) / lnbeta : R(0);
-  R s = region_guess<R>(region, nd, lnbeta);
-  for (int i = 0; i < steps; ++i) s = householder_step<R>(nd.x, nd.bb, lnbetac, inv_lnbeta, region, s);
-  return s;
-}
 
 // The final FP64 step of the mixed form.  Its iterate comes from the float
 // solve (within ~1e-6 relative), so every region takes the Newton ratio of
@@ -715,21 +715,6 @@ __device__ __forceinline__ double solve_deep_mixed64(double x, double bmax, doub
   return fabs(s - double(sf)) <= kDeepAccept * s ? s : __longlong_as_double(0x7ff8000000000000LL);
 }
 
-// Mixed precision (PIVOT_MODE_MIXED): the float node seeds a float guess and
-// `steps - 1` float Householder steps; the final step runs in double from
-// the double inputs of the row (x, beta or beta_c, ln beta).  Householder(3)
-// converges quartically, so a float iterate within ~1e-4 relative lands at
-// double precision after the one FP64 step.
-__device__ __forceinline__ double solve_region_mixed(int region, const Node<float>& nf, double x, double bb,
-                                                     double lnbeta, int steps) {
-  const float lnbetac_f = (region == kUpper) ? logf(nf.bb) : 0.0f;
-  const float inv_lnbeta_f = (region == kLower) ? 1.0f / float(lnbeta) : 0.0f;
-  float sf = region_guess<float>(region, nf, float(lnbeta));
-  for (int i = 1; i < steps; ++i) sf = householder_step<float>(nf.x, nf.bb, lnbetac_f, inv_lnbeta_f, region, sf);
-  const double lnbetac = (region == kUpper) ? log(bb) : 0.0;
-  const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
-  return householder_step<double>(x, bb, lnbetac, inv_lnbeta, region, double(sf));
-}
 
 // ---------------------------------------------------------------------------
 // Adjoint (Eq. implicit_iv / method_vjp) with the low-vega gate (Section 3.3).
