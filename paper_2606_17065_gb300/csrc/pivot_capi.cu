@@ -129,12 +129,15 @@ struct TileCfg {
   // six node fields per row (+ e^{r tau}, e^{(r-q) tau} in the Black-Scholes form), two row lists
   static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
 };
-// Region bins: 4 in the FP64 form.  The mixed form has 4 float-seeded region
-// bins, 4 FP64 bins for rows outside the float range (b_max - beta below
-// kMixedFloor, |x| above kMixedMaxAbsX, or beta below kMixedFloor near the
-// money), and bin kDeepBin: lower-tail rows with beta below kMixedFloor and
-// |x| >= kDeepMinAbsX, seeded in float from ln beta (float_deep_seed).
-constexpr int kMaxBins = 9;
+// Region bins.  FP64 form: the 4 regions, plus 2 bins for middle-region rows
+// near the money (|x| <= kTaylorX), the only rows whose b may take the
+// Taylor series of rho: kept apart, a warp runs one of the two forms of rho.
+// Mixed form: 4 float-seeded region bins, 4 FP64 bins for rows outside the
+// float range (b_max - beta below kMixedFloor, |x| above kMixedMaxAbsX, or
+// beta below kMixedFloor near the money), bin kDeepBin (lower-tail rows with
+// beta below kMixedFloor and |x| >= kDeepMinAbsX, seeded in float from
+// ln beta), and 2 near-the-money float bins.
+constexpr int kMaxBins = 11;
 constexpr int kDeepBin = 8;
 constexpr double kMixedFloor = 1e-30;
 constexpr double kMixedMaxAbsX = 80.0;
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
   uint16_t* s_list = reinterpret_cast<uint16_t*>(s_ec + (kBS ? kTile : 0));  // phase 1 -> 2: rows to solve
   uint16_t* s_order = s_list + kTile;                                        // phase 2 -> 3: region order
   __shared__ int s_nsolve;
-  constexpr int kBins = kMixed ? 9 : 4;
+  constexpr int kBins = kMixed ? 11 : 6;
   __shared__ int s_cnt[kMaxBins];
   __shared__ int s_off[kMaxBins + 1];
 
@@ -271,6 +274,11 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
           s_bsn[r] = nd.bsn;
           s_bb[r] = nd.bb;
         }
+        // middle rows near the money to their own bins (FP64 form: 1, 2 -> 4, 5; mixed float: 1, 2 -> 9, 10)
+        if (x >= -pivot::kTaylorX) {
+          if (!kMixed && (rg == pivot::kMidLow || rg == pivot::kMidHigh)) rg += 3;
+          if (kMixed && !fp64_row && (rg == pivot::kMidLow || rg == pivot::kMidHigh)) rg += 8;
+        }
         row[j] = r;
       }
       reg[j] = rg;
@@ -304,8 +312,9 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
       row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
       const int fl = a.flag[i];
       const bool deep = kMixed && bin == kDeepBin;
-      const int rg = deep ? int(pivot::kLower) : (bin & 3);
-      const bool float_row = kMixed && (bin < 4 || deep);
+      const int rg = kMixed ? (deep ? int(pivot::kLower) : bin > kDeepBin ? bin - 8 : (bin & 3))
+                            : (bin < 4 ? bin : bin - 3);
+      const bool float_row = kMixed && (bin < 4 || bin >= kDeepBin);
       const double bb = s_bb[r];
       // ln beta for the FP64 solve of a lower-region row (the float-seeded rows of the mixed form do without)
       const double lnbeta = (rg == pivot::kLower && !float_row) ? pivot::log_beta(bb, F, K, T, P, fl) : 0.0;
@@ -324,7 +333,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
           const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, P, fl) : 0.0;
           s = pivot::solve64(rg2, nd, lnb2, a.steps, last);
         }
-      } else if (kMixed && bin < 4) {
+      } else if (float_row) {
         pivot::Node<float> nf;
         const float2 p0 = *reinterpret_cast<const float2*>(&s_e[r]);
         const float2 p1 = *reinterpret_cast<const float2*>(&s_bn[r]);

@@ -529,16 +529,17 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   last.ya = ya;
   last.yb = yb;
   last.lbs = lbs;
-  last.ibs = 0.0;
   // 1/b_s where the middle objective or the larger ratio of the pair needs it
   const bool need_ibs = region == kMidLow || region == kMidHigh || (region == kLower ? hpt > 0.0 : hpt <= 0.0);
   double ibs = need_ibs ? exp(-lbs) : 0.0;
   double E1 = bmax * ibs;
   double beta_ibs = beta * ibs;
+  last.ibs = need_ibs ? ibs : 0.0; // for adjoint_reuse (0: not formed)
   if (!(ibs < INFINITY)) {
     // b_s below ~1e-308 (|ln(F/K)| beyond ~1400): the products in logarithms
     E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
     beta_ibs = exp(log(beta) - lbs);
+    last.ibs = 0.0;
   }
   double nu, L = 0.0, q = 0.0, iL = 0.0;
   if (region == kUpper) {
