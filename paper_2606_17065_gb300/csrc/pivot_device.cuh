@@ -97,6 +97,7 @@ __device__ __forceinline__ double erfcx_fp64(double a) {
 template <>
 struct Math<double> {
   static __device__ __forceinline__ double erfcx_(double v) { return erfcx_fp64(v); }
+  static __device__ __forceinline__ double erfcx_pos_(double v) { return erfcx_nonneg(v); } // v >= 0
   static __device__ __forceinline__ double exp_(double v) { return ::exp(v); }
   static __device__ __forceinline__ double log_(double v) { return ::log(v); }
   static __device__ __forceinline__ double sqrt_(double v) { return ::sqrt(v); }
@@ -111,6 +112,7 @@ struct Math<double> {
 template <>
 struct Math<float> {
   static __device__ __forceinline__ float erfcx_(float v) { return ::erfcxf(v); }
+  static __device__ __forceinline__ float erfcx_pos_(float v) { return ::erfcxf(v); }
   static __device__ __forceinline__ float exp_(float v) { return ::expf(v); }
   static __device__ __forceinline__ float log_(float v) { return ::logf(v); }
   static __device__ __forceinline__ float sqrt_(float v) { return ::sqrtf(v); }
@@ -378,7 +380,6 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
   const R x = nd.x, ax = -x;
   const R sc = M::sqrt_(R(2) * ax);
   const R e = nd.e;
-  const R dc = R(kSqrt2Pi) / nd.bmax; // ds/db at s_c
   switch (region) {
     case kLower: {
       // lower tail: b ~ kappa Phi(-|x|/(sqrt3 s))^3 as s -> 0, kappa = 2 pi |x| / (3 sqrt 3).
@@ -386,13 +387,13 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       // (G(0) = 0, G'(0) = 1, G(u_l), G'(u_l) exact), then invert G for s.
       const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
       const R bl = nd.bn, bsl = nd.bsn, beta = nd.bb;
-      const R kap = R(kTwoPiOver3Sqrt3) * ax;
-      const R u = (beta > M::kTiny) ? M::cbrt_(beta / kap) : M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
-      const R ul = M::cbrt_(bl / kap);
+      const R kap = R(kTwoPiOver3Sqrt3) * ax, inv_kap = R(1) / kap;
+      const R u = (beta > M::kTiny) ? M::cbrt_(beta * inv_kap) : M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
+      const R ul = M::cbrt_(bl * inv_kap);
       const R al = ax * R(kInvSqrt3) / sl;
       // Phi(-al) = phi(al) Y(-al) = exp(-al^2/2) erfcx(al/sqrt 2) / 2: one exponential shared with phi(al)
       const R eal = M::exp_(R(-0.5) * al * al);
-      const R Gl = R(0.5) * eal * M::erfcx_(al * R(kInvSqrt2));
+      const R Gl = R(0.5) * eal * M::erfcx_pos_(al * R(kInvSqrt2));
       const R dGl = R(3) * bl * (R(kInvSqrt2Pi) * eal) * al / (sl * ul * bsl);
       const R r = shape_monotone<R>(ul, R(0), Gl, R(1), dGl);
       const R G = M::fmin_(rational_cubic<R>(u, R(0), ul, R(0), Gl, R(1), dGl, r), R(0.5));
@@ -400,6 +401,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
     }
     case kMidLow: {
       // rational cubic in b on [b_l, b_c], zero curvature of s(b) at the inflection b_c
+      const R dc = R(kSqrt2Pi) / nd.bmax; // ds/db at s_c
       const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
       const R bc = R(0.5) * nd.bmax * (R(1) - e);
       const R bl = nd.bn;
@@ -411,6 +413,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
     }
     case kMidHigh: {
       // rational cubic in b on [b_c, b_u], zero curvature of s(b) at b_c
+      const R dc = R(kSqrt2Pi) / nd.bmax;
       const R su = sc + R(kSqrtPiOver2) * (R(1) + e);
       const R bc = R(0.5) * nd.bmax * (R(1) - e);
       const R bu = nd.bmax - nd.bn;
@@ -426,7 +429,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R uu = R(0.5) * nd.bn;
       // Phi(-su/2) and phi(su/2) from one exponential, as in the lower region
       const R esu = M::exp_(R(-0.125) * su * su);
-      const R vu = R(0.5) * esu * M::erfcx_(su * R(0.5 * kInvSqrt2));
+      const R vu = R(0.5) * esu * M::erfcx_pos_(su * R(0.5 * kInvSqrt2));
       const R dvu = (R(kInvSqrt2Pi) * esu) / nd.bsn;
       const R r = shape_monotone<R>(uu, R(0), vu, R(1), dvu);
       const R v = M::fmin_(rational_cubic<R>(R(0.5) * nd.bb, R(0), uu, R(0), vu, R(1), dvu, r), R(0.5));

@@ -351,12 +351,14 @@ def test_extreme_moneyness():
     P, _ = oracle.black_price(F, K, T, S, flag)
     ref, st_ref = oracle.implied_vol(F, K, T, P, flag)
     assert (st_ref == 0).sum() >= 24  # in-the-money rows collapse onto a bound at these scales
-    sig, st = pv.iv(to_dev(F), to_dev(K), to_dev(T), to_dev(P), to_dev(flag))
-    sig, st = to_np(sig), to_np(st)
-    dom = assert_sigma_parity(F, K, T, P, flag, sig, st, ref, st_ref, where="extreme")
-    for mode in (0, 1):
-        out = pv.iv_forward_backward(to_dev(F), to_dev(K), to_dev(T), to_dev(P), to_dev(flag), tau=1e-300,
-                                     gate=mode)
-        want = oracle.iv_grad(F, K, T, flag, ref, None, 1e-300, mode)
-        _, Vr = oracle.black_price(F, K, T, np.where(np.isfinite(ref), ref, 1.0), flag)
-        assert_grad_parity([to_np(x) for x in out[2:]], want, dom, where=f"extreme mode={mode}", vega=Vr)
+    for form in ("fp64", "mixed"):
+        sig, st = pv.iv(to_dev(F), to_dev(K), to_dev(T), to_dev(P), to_dev(flag), mode=form)
+        sig, st = to_np(sig), to_np(st)
+        dom = assert_sigma_parity(F, K, T, P, flag, sig, st, ref, st_ref, where=f"extreme {form}")
+        for mode in (0, 1):
+            out = pv.iv_forward_backward(to_dev(F), to_dev(K), to_dev(T), to_dev(P), to_dev(flag), tau=1e-300,
+                                         gate=mode, mode=form)
+            want = oracle.iv_grad(F, K, T, flag, ref, None, 1e-300, mode)
+            _, Vr = oracle.black_price(F, K, T, np.where(np.isfinite(ref), ref, 1.0), flag)
+            assert_grad_parity([to_np(x) for x in out[2:]], want, dom, where=f"extreme {form} gate={mode}",
+                               vega=Vr)
