@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
       pivot::Last last;
       if (deep) {
         s = pivot::solve_deep_mixed64(s_x[r], s_bmax[r], bb, last);
-        if (!(s > 0.0 && s < INFINITY)) {
+        if (!pivot::pos_finite(s)) {
           // not accepted: the FP64 path from the row's inputs
           const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
           double x, bmax;
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
         nf.bmax = p2.x;
         nf.bb = p2.y;
         s = pivot::solve_mixed64(rg, nf, s_x[r], s_bmax[r], bb, a.steps, last);
-        if (!(s > 0.0 && s < INFINITY)) {
+        if (!pivot::pos_finite(s)) {
           // float seed failed: redo the row in double from its inputs
           const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
           double x, bmax;

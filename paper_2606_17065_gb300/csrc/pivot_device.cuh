@@ -60,9 +60,14 @@ struct Math;
 #include "erfcx_table.inc"
 
 __device__ __forceinline__ double erfcx_nonneg(double a) {
-  if (a < 16.0) {
-    const double fi = floor(a * 8.0);
-    const double* c = kErfcxCoef[int(fi)];
+  if ((uint64_t(__double_as_longlong(a)) & 0x7fffffffffffffffull) < 0x4030000000000000ull) { // |a| < 16 (a = -0 too)
+    // interval k = floor(8a) from the rounding of (8a - 1/2) + 1.5 2^52 (ulp 1 there; 8a - 1/2
+    // is exact): k sits in the low mantissa bits, so neither a floor nor a conversion runs on
+    // the FP64 pipe (an exact 8a = k + 1 may land on k with tau = 1, the interval's end)
+    const double tr = fma(a, 8.0, -0.5) + 6755399441055744.0;
+    const int k = int(uint64_t(__double_as_longlong(tr)) & 127ull);
+    const double fi = tr - 6755399441055744.0;
+    const double* c = kErfcxCoef[k];
     const double tau = fma(a - fi * 0.125, 16.0, -1.0);
     double v = __ldg(c + 9);
 #pragma unroll
@@ -242,8 +247,9 @@ __device__ __forceinline__ bool neg64(double v) {
 }
 // v == 0 (either sign)
 __device__ __forceinline__ bool zero64(double v) { return (uint64_t(__double_as_longlong(v)) << 1) == 0ull; }
-// a > b for positive finite a, b: their bit patterns order as integers
+// a > b (a <= b) for non-negative finite a, b: their bit patterns order as integers
 __device__ __forceinline__ bool gt_pos(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
+__device__ __forceinline__ bool le_pos(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
 
 __device__ __forceinline__ bool bad_inputs(double F, double K, double T, int flag) {
   // also rejects NaN and +-inf
@@ -275,7 +281,8 @@ __device__ __forceinline__ double neg_abs_log_ratio(double mn, double mx, double
 // x = -|ln(F/K)|, b_max = e^{x/2} = sqrt(min/max)
 __device__ __forceinline__ void moneyness(double F, double K, double& x, double& bmax) {
   double r;
-  x = neg_abs_log_ratio(fmin(F, K), fmax(F, K), &r);
+  const bool fk = gt_pos(F, K); // F, K positive: integer order of the bit patterns
+  x = neg_abs_log_ratio(fk ? K : F, fk ? F : K, &r);
   bmax = sqrt(r);
 }
 
@@ -520,7 +527,7 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   const double inv_s = 1.0 / s;
   const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
   const double lbs = log_bs<double>(h, t);
-  const bool taylor = region != kUpper && t <= kTaylorT && x >= -kTaylorX;
+  const bool taylor = region != kUpper && le_pos(t, kTaylorT) && le_pos(-x, kTaylorX);
   last.za = -fabs(hpt);
   last.zb = h - t;
   last.pair = !taylor;
@@ -538,7 +545,7 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   double E1 = bmax * ibs;
   double beta_ibs = beta * ibs;
   last.ibs = need_ibs ? ibs : 0.0; // for adjoint_reuse (0: not formed)
-  if (!(ibs < INFINITY)) {
+  if (!finite64(ibs)) {
     // b_s below ~1e-308 (|ln(F/K)| beyond ~1400): the products in logarithms
     E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
     beta_ibs = exp(log(beta) - lbs);
@@ -615,7 +622,7 @@ __device__ __forceinline__ double step64_final(double x, double bmax, double bb,
   const double inv_s = 1.0 / s;
   const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
   const double lbs = log_bs<double>(h, t);
-  const bool taylor = region != kUpper && t <= kTaylorT && x >= -kTaylorX;
+  const bool taylor = region != kUpper && le_pos(t, kTaylorT) && le_pos(-x, kTaylorX);
   last.za = -fabs(hpt);
   last.zb = h - t;
   last.pair = !taylor;
@@ -838,7 +845,7 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   const double yb = near ? mills_shift(last.yb, last.zb, zb - last.zb) : mills_small(zb);
   const double lbs = log_bs<double>(h, t);
   double ibs;
-  if (last.ibs > 0.0 && fabs(lbs - last.lbs) < 1e-3) {
+  if (__double_as_longlong(last.ibs) > 0 && fabs(lbs - last.lbs) < 1e-3) {
     // 1/b_s from the last step's: exp(-d) to third order, d = lbs - last.lbs (|d| < 1e-3: d^4/24 < 5e-14)
     const double d = lbs - last.lbs;
     ibs = last.ibs * fma(fma(fma(d, -1.0 / 6.0, 0.5), d, -1.0), d, 1.0);

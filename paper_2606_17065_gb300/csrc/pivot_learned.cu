@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
         pivot::Last last;
         const double x = S.x[r], bmax = S.bmax[r];
         const double s = pivot::solve_deep_mixed64(x, bmax, S.bb[r], last);
-        if (s > 0.0 && s < INFINITY) {
+        if (pivot::pos_finite(s)) {
           const int64_t i = base + r;
           finish_row<kBackward>(a, i, a.F[i], a.K[i], a.T[i], a.flag[i], s, x, bmax, last);
         } else {
