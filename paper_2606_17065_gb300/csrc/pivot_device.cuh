@@ -112,7 +112,9 @@ struct Math<double> {
   static __device__ __forceinline__ double fma_(double a, double b, double c) { return ::fma(a, b, c); }
   static __device__ __forceinline__ double fmin_(double a, double b) { return ::fmin(a, b); }
   static __device__ __forceinline__ double fmax_(double a, double b) { return ::fmax(a, b); }
-  static constexpr double kTiny = 1e-280; // below this beta's cube root is taken through logs
+  static constexpr double kTiny = 1e-290;     // below this a cube root argument is scaled
+  static constexpr double kScaleUp = 0x1p300;  // 2^300
+  static constexpr double kScaleDown = 0x1p-100; // its cube root, inverted
 };
 template <>
 struct Math<float> {
@@ -128,6 +130,8 @@ struct Math<float> {
   static __device__ __forceinline__ float fmin_(float a, float b) { return ::fminf(a, b); }
   static __device__ __forceinline__ float fmax_(float a, float b) { return ::fmaxf(a, b); }
   static constexpr float kTiny = 1e-35f;
+  static constexpr float kScaleUp = 0x1p60f;
+  static constexpr float kScaleDown = 0x1p-20f;
 };
 
 // Y(z) = Phi(z)/phi(z).  Kept out of line: it is called from many sites and
@@ -395,7 +399,12 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
       const R bl = nd.bn, bsl = nd.bsn, beta = nd.bb;
       const R kap = R(kTwoPiOver3Sqrt3) * ax, inv_kap = R(1) / kap;
-      const R u = (beta > M::kTiny) ? M::cbrt_(beta * inv_kap) : M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
+      // u = (beta/kappa)^(1/3); below ~1e-290 the cube root of the argument scaled by 2^300 times
+      // 2^-100 (exact scalings, no branch), and through ln beta only where beta/kappa underflowed
+      const R v = beta * inv_kap;
+      const bool tiny = v < M::kTiny;
+      R u = M::cbrt_(tiny ? v * M::kScaleUp : v) * (tiny ? M::kScaleDown : R(1));
+      if (__builtin_expect(!(v > R(0)), 0)) u = M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
       const R ul = M::cbrt_(bl * inv_kap);
       const R al = ax * R(kInvSqrt3) / sl;
       // Phi(-al) = phi(al) Y(-al) = exp(-al^2/2) erfcx(al/sqrt 2) / 2: one exponential shared with phi(al)
