@@ -131,7 +131,10 @@ struct TileCfg {
 };
 // Region bins.  FP64 form: the 4 regions, plus 2 bins for middle-region rows
 // near the money (|x| <= kTaylorX), the only rows whose b may take the
-// Taylor series of rho: kept apart, a warp runs one of the two forms of rho.
+// Taylor series of rho: kept apart, a warp runs one of the two forms of rho;
+// and bin 6 for lower-region rows with beta below kDeepBeta, whose Mills
+// ratios (|h -+ t| beyond ~20 at ln beta ~ -h^2/2) take erfcx's asymptotic
+// series rather than its table.
 // Mixed form: 4 float-seeded region bins, 4 FP64 bins for rows outside the
 // float range (b_max - beta below kMixedFloor, |x| above kMixedMaxAbsX, or
 // beta below kMixedFloor near the money), bin kDeepBin (lower-tail rows with
@@ -139,6 +142,7 @@ struct TileCfg {
 // ln beta), and 2 near-the-money float bins.
 constexpr int kMaxBins = 11;
 constexpr int kDeepBin = 8;
+constexpr double kDeepBeta = 1e-100;
 constexpr double kMixedFloor = 1e-30;
 constexpr double kMixedMaxAbsX = 80.0;
 constexpr double kDeepMinAbsX = 0.1;
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
   uint16_t* s_list = reinterpret_cast<uint16_t*>(s_ec + (kBS ? kTile : 0));  // phase 1 -> 2: rows to solve
   uint16_t* s_order = s_list + kTile;                                        // phase 2 -> 3: region order
   __shared__ int s_nsolve;
-  constexpr int kBins = kMixed ? 11 : 6;
+  constexpr int kBins = kMixed ? 11 : 7;
   __shared__ int s_cnt[kMaxBins];
   __shared__ int s_off[kMaxBins + 1];
 
@@ -279,6 +283,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
           if (!kMixed && (rg == pivot::kMidLow || rg == pivot::kMidHigh)) rg += 3;
           if (kMixed && !fp64_row && (rg == pivot::kMidLow || rg == pivot::kMidHigh)) rg += 8;
         }
+        if (!kMixed && rg == pivot::kLower && beta < kDeepBeta) rg = 6;
         row[j] = r;
       }
       reg[j] = rg;
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
       const int fl = a.flag[i];
       const bool deep = kMixed && bin == kDeepBin;
       const int rg = kMixed ? (deep ? int(pivot::kLower) : bin > kDeepBin ? bin - 8 : (bin & 3))
-                            : (bin < 4 ? bin : bin - 3);
+                            : (bin < 4 ? bin : bin == 6 ? int(pivot::kLower) : bin - 3);
       const bool float_row = kMixed && (bin < 4 || bin >= kDeepBin);
       const double bb = s_bb[r];
       // ln beta for the FP64 solve of a lower-region row (the float-seeded rows of the mixed form do without)
