@@ -169,10 +169,22 @@ def max_over_ranks(value, world):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_rate(target_seconds: float, seed: int = 2):
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_rate(target_seconds: float, seed: int = 2, threads: int | None = None):
     """Forward+backward rows/s of the CPU oracle on a bounded sample of the stress workload."""
     import oracle
-    threads = oracle.max_threads()
+    threads = threads or oracle.max_threads()
     pilot = workloads.stress_batch(4096, seed=seed + 1000)
     P, _ = oracle.black_price(pilot.F, pilot.K, pilot.T, pilot.sigma_star, pilot.flag, nthreads=threads)
     P = workloads.merge_prices(pilot, P)
@@ -490,11 +502,33 @@ def run_ours(args, rank, world):
     body = body_variants(dev, stream, max(args.steps // 4, 2)) if args.rows == workloads.STRESS_N else None
     bsv = bs_variants(dev, stream, max(args.steps // 4, 2)) if args.rows == workloads.STRESS_N else None
 
+    # configuration 1: 4,096 rows, one launch (launch- and latency-bound, not a throughput line)
+    small = workloads.body_batch(workloads.SMALL_N, seed=1)
+    sF, sK, sT = (torch.from_numpy(a).to(dev) for a in (small.F, small.K, small.T))
+    sflag = torch.from_numpy(small.flag).to(dev)
+    sP, _ = pv.black_price(sF, sK, sT, torch.from_numpy(small.sigma_star).to(dev), sflag, vega=False)
+    sout = [torch.empty(small.n, dtype=torch.float64, device=dev) for _ in range(5)]
+    sst = torch.empty(small.n, dtype=torch.uint8, device=dev)
+
+    def small_step():
+        rc = lib.pivot_iv_forward_backward(small.n, p(sF), p(sK), p(sT), p(sP), p(sflag), None, TAU,
+                                           pv.GATES[GATE], p(sout[0]), p(sst), *[p(g) for g in sout[1:]],
+                                           ctypes.byref(opts), sptr)
+        if rc != 0:
+            raise RuntimeError(_native.error_string(rc))
+
+    opts.mode = 0
+    small_line = time_variant(small_step, small.n, stream, 50)
+    small_line["note"] = "4,096 body rows per launch: launch- and latency-bound"
+
     cpu = None
     if rank == 0 and world == 1:
         r, threads, m, dt = oracle_rate(args.cpu_seconds)
+        r1, _, m1, dt1 = oracle_rate(max(args.cpu_seconds / 4, 0.5), threads=1)
         cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{m} seeded rows of the same stress workload, fwd+bwd, {dt:.1f} s wall"}
+               "sample": f"{m} seeded rows of the same stress workload, fwd+bwd, {dt:.1f} s wall",
+               "cpu_model": cpu_model(),
+               "single_thread": {"value": r1, "unit": UNIT, "sample": f"{m1} rows, {dt1:.1f} s wall"}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -510,6 +544,7 @@ def run_ours(args, rank, world):
                 "forward_only": {"value": n * world / (fwd_ms * 1e-3), "unit": UNIT, "ms_per_step": fwd_ms},
                 "variants": {"mixed_same_workload": mixed,
                              "mixed_speedup_same_workload": ms_per_step / mixed["ms_per_step"],
+                             "config1_4096": small_line,
                              "body_64M": body,
                              "black_scholes_16M": bsv},
                 "cpu_baseline": cpu}
