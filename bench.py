@@ -46,7 +46,7 @@ BYTES_PER_ROW = 33 + 41
 # launch of the same distribution does the same work per row on average.
 FLOPS_PER_ROW = 467.8
 # dram__bytes_read.sum + dram__bytes_write.sum per row from the same capture.
-TRAFFIC_PER_ROW = 93.03
+TRAFFIC_PER_ROW = 93.87
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA lanes/clk x 2 FLOP
 # (= 1.25 TFLOP/s nominal at 2.07 GHz), scaled by the SM clock seen under load.
 SMS = 152
@@ -170,6 +170,13 @@ def max_over_ranks(value, world):
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
