@@ -74,16 +74,18 @@ def _host_result(inputs, outs):
 
 
 # Host inputs of more than this many rows are streamed through the device in
-# chunks of this size on two CUDA streams, so that the copies of one chunk
-# overlap the kernels of the other.
+# chunks of this size on three CUDA streams, so that the host-to-device copy of
+# one chunk, the kernels of the next and the device-to-host copy of a third
+# overlap.
 HOST_CHUNK = 1 << 21
+HOST_STREAMS = 3
 _streams = {}
 
 
 def _copy_streams(device):
     key = device.index
     if key not in _streams:
-        _streams[key] = (torch.cuda.Stream(device), torch.cuda.Stream(device))
+        _streams[key] = tuple(torch.cuda.Stream(device) for _ in range(HOST_STREAMS))
     return _streams[key]
 
 
@@ -105,7 +107,7 @@ def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args):
     arguments for m rows of device tensors, stream excluded.  Device inputs
     run in place on the current stream; host inputs larger than HOST_CHUNK are
     pipelined chunk by chunk (host -> device, kernel, device -> host on
-    alternating streams) into pinned host outputs."""
+    rotating streams) into pinned host outputs."""
     n = next(t for t in inputs if t is not None)
     n = n.numel() if isinstance(n, torch.Tensor) else len(n)
     if not _is_host(inputs) or n <= HOST_CHUNK:
@@ -127,8 +129,8 @@ def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args):
         st.wait_stream(main)
     for k, lo in enumerate(range(0, n, HOST_CHUNK)):
         m = min(HOST_CHUNK, n - lo)
-        st = streams[k % 2]
-        dins, douts = bufs[k % 2]
+        st = streams[k % len(streams)]
+        dins, douts = bufs[k % len(streams)]
         with torch.cuda.stream(st):
             ins = [None if h is None else d[:m] for d, h in zip(dins, hins)]
             for d, h in zip(ins, hins):

@@ -103,8 +103,9 @@ __global__ void __launch_bounds__(kBlock) k_bs_iv_backward(Args a) {
 
 // ---------------------------------------------------------------------------
 // Forward (and fused forward+backward) with per-tile compaction and region
-// binning.  A block owns a tile of kTile consecutive rows.
-//  phase 1: every thread classifies kTile/kBlock rows (coalesced loads) with
+// binning.  A block owns a tile of consecutive rows (kTile, or fewer on a batch
+// too small to give every resident block a full tile).
+//  phase 1: every thread classifies tile/kBlock rows (coalesced loads) with
 //           the cheap stage-1 tests; rows that need no solve (invalid, or at
 //           a bound of the price interval) are finished at once, the others
 //           are appended to a tile-local list (one warp-aggregated atomic).
@@ -117,14 +118,14 @@ __global__ void __launch_bounds__(kBlock) k_bs_iv_backward(Args a) {
 // The grid is persistent: blocks stride over tiles.
 // ---------------------------------------------------------------------------
 // Tile rows per block: 2,048 for the Black-76 forms (2 blocks of 256 threads
-// per SM, 106,496 B of shared memory each), 1,024 for the Black-Scholes form,
+// per SM, 106,496 B of shared memory each), 1,536 for the Black-Scholes form,
 // whose two extra doubles per row would not let two 2,048-row blocks fit
-// (3 blocks of 69,632 B).  Larger tiles pack the region bins of phase 3 into
-// fewer partially filled warps.
+// (2 blocks of 104,448 B).  Larger tiles pack the region bins of phase 3 into
+// fewer partially filled warps; 2 blocks per SM leave ~128 registers a thread.
 template <bool kBS>
 struct TileCfg {
-  static constexpr int kTile = kBS ? 1024 : 2048;
-  static constexpr int kMinBlocks = kBS ? 3 : 2;
+  static constexpr int kTile = kBS ? 1536 : 2048;
+  static constexpr int kMinBlocks = 2;
   static constexpr int kRowsPerThread = kTile / kBlock;
   // six node fields per row (+ e^{r tau}, e^{(r-q) tau} in the Black-Scholes form), two row lists
   static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
@@ -185,7 +186,11 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  for (int64_t base = int64_t(blockIdx.x) * kTile; base < a.n; base += int64_t(gridDim.x) * kTile) {
+  // rows per tile for this launch: the launcher shrinks tiles on small batches so that
+  // every SM gets work; the shared arrays keep their kTile strides
+  const int tile = a.tile;
+  const int jmax = tile / kBlock;
+  for (int64_t base = int64_t(blockIdx.x) * tile; base < a.n; base += int64_t(gridDim.x) * tile) {
     if (tid < kBins) s_cnt[tid] = 0;
     if (tid == 0) s_nsolve = 0;
     __syncthreads();
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
       const int r = j * kBlock + tid;
       const int64_t i = base + r;
       bool solve = false;
-      if (i < a.n) {
+      if (j < jmax && i < a.n) {
         const double K = a.K[i], T = a.T[i];
         double rr = 0.0, qq = 0.0;
         if (kBS) {
@@ -437,10 +442,16 @@ int launch_binned(const Args& a, void* stream) {
     blocks_per_sm = b < 1 ? 1 : b;
     configured_device = dev;
   }
-  const int64_t tiles = (a.n + kTile - 1) / kTile;
   const int64_t cap = int64_t(blocks_per_sm) * num_sms;
+  // the largest tile (a multiple of the block) that still gives every resident block a tile
+  int64_t tile = (a.n + cap - 1) / cap;
+  tile = ((tile + kBlock - 1) / kBlock) * kBlock;
+  if (tile > kTile) tile = kTile;
+  Args b = a;
+  b.tile = int(tile);
+  const int64_t tiles = (a.n + tile - 1) / tile;
   const unsigned grid = unsigned(tiles < cap ? tiles : cap);
-  k_iv_binned<kBackward, kMixed, kBS><<<grid, kBlock, smem, static_cast<cudaStream_t>(stream)>>>(a);
+  k_iv_binned<kBackward, kMixed, kBS><<<grid, kBlock, smem, static_cast<cudaStream_t>(stream)>>>(b);
   return launch_status();
 }
 

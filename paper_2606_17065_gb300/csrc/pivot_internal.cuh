@@ -29,6 +29,9 @@ struct Args {
   // dP / dF / dT receive dsigma/dV, dsigma/dS, dsigma/dtau; r, q per row
   const double *r, *q;
   double *dr, *dq;
+  // rows per tile of the binned kernel (a multiple of its block size, at most
+  // its compile-time tile); 0 = the largest; set by the launcher
+  int tile;
 };
 
 __device__ __forceinline__ void write_grad(const Args& a, int64_t i, double F, double K, double T, int fl,
