@@ -233,6 +233,16 @@ int pivot_bs_iv_forward_backward(int64_t n, const double* S, const double* K, co
 int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream);
 
 /*
+ * pivot_elementary -- the library's table-driven FP64 logarithm (fn = 0) and
+ * exponential (fn = 1), which the solver uses for ln b, ln beta, 1/b_s and
+ * the seeds (P. T. P. Tang's method; within 1 ulp).
+ *   in : x (n float64)   out: y (n float64)
+ * Exposed so that they can be checked on their own; fn outside {0, 1} is
+ * PIVOT_E_OPTS.
+ */
+int pivot_elementary(int32_t fn, int64_t n, const double* x, double* y, void* stream);
+
+/*
  * Training of the learned initial guess with the library's own kernels
  * (BF16 tensor-core forward and backward, FP32 accumulation).  The training
  * pairs are the operator's own: quotes (F, K, T, P, flag) and the sigma that

@@ -35,6 +35,7 @@ _SIGNATURES = {
     "pivot_bs_iv_backward": [c_i64] + [c_vp] * 8 + [c_dbl, ctypes.c_int32] + [c_vp] * 7,
     "pivot_bs_iv_forward_backward": [c_i64] + [c_vp] * 8 + [c_dbl, ctypes.c_int32] + [c_vp] * 10,
     "pivot_mills_ratio": [c_i64, c_vp, c_vp, c_vp],
+    "pivot_elementary": [c_i32, c_i64, c_vp, c_vp, c_vp],
     "pivot_mlp_trainer_bytes": [c_vp],
     "pivot_iv_guess": [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
     "pivot_mlp_init": [c_vp, ctypes.c_uint64, c_vp],

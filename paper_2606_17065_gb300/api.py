@@ -187,6 +187,15 @@ def mills_ratio(z):
     return _host_result((z,), [y])[0]
 
 
+def elementary(fn: str, x):
+    """The library's FP64 log (fn="log") or exp (fn="exp"), evaluated by its kernel."""
+    dev = _device_of(x)
+    xx = _on(x, dev, torch.float64)
+    y = torch.empty_like(xx)
+    _native.call("pivot_elementary", {"log": 0, "exp": 1}[fn], xx.numel(), _p(xx), _p(y), _stream(dev))
+    return _host_result((x,), [y])[0]
+
+
 def _opts(mode, householder, mlp=None, fallback: float = 0.0):
     o = _native.PivotOpts()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)

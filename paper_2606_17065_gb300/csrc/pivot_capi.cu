@@ -46,6 +46,13 @@ __global__ void __launch_bounds__(kBlock) k_black_price_backward(
   }
 }
 
+__global__ void __launch_bounds__(kBlock) k_elementary(int fn, int64_t n, const double* __restrict__ x,
+                                                        double* __restrict__ y) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = fn == 0 ? pivot::log_fp64(x[i]) : pivot::exp_fp64(x[i]);
+}
+
 __global__ void __launch_bounds__(kBlock) k_mills_ratio(int64_t n, const double* __restrict__ z,
                                                         double* __restrict__ y) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -660,6 +667,19 @@ int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream) {
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
   k_mills_ratio<<<grid_for(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(n, z, y);
+  return launch_status();
+}
+
+int pivot_elementary(int32_t fn, int64_t n, const double* x, double* y, void* stream) {
+  if (fn != 0 && fn != 1) return PIVOT_E_OPTS;
+  if (n < 0) return PIVOT_E_SIZE;
+  if (n == 0) return PIVOT_OK;
+  int dev = -1;
+  const Ptr ps[] = {{x, true, true}, {y, true, true}};
+  int rc = check_all(ps, &dev);
+  if (rc == PIVOT_OK) rc = select_device(dev);
+  if (rc != PIVOT_OK) return rc;
+  k_elementary<<<grid_for(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(fn, n, x, y);
   return launch_status();
 }
 

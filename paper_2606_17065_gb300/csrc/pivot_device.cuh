@@ -89,11 +89,67 @@ __device__ __forceinline__ double erfcx_nonneg(double a) {
   return s * ia * 0.564189583547756286948; // 1/sqrt(pi)
 }
 
+// Table-driven FP64 logarithm and exponential (P. T. P. Tang's method, ACM TOMS
+// 16(4) 1990 and 15(2) 1989; tables by gen_elementary_tables.py).  Both are
+// within 1 ulp and run almost wholly as fma on the FP64 pipe: the table
+// index and the exponent come from bit patterns and the rounding of a value
+// plus 1.5 2^52, not from floor or conversion instructions.
+//   log: v = 2^e m, c = 1 + j/128 nearest m (j in [0, 128]), f = (m - c)/c,
+//        ln v = (e ln2_hi + ln c_hi) + (e ln2_lo + ln c_lo + ln(1 + f)),
+//        ln(1 + f) to degree 7 (|f| <= 1/256); the hi sum is exact, and near
+//        v = 1 (j = 0, or j = 128 with e = -1) both sums reduce to ln(1 + f).
+//   exp: v = n ln2/128 + r, |r| <= ln2/256: e^v = 2^(n >> 7) 2^((n & 127)/128) e^r,
+//        e^r - 1 to degree 5.
+// Inputs outside their plain range (log: not positive normal finite; exp:
+// |v| >= 708) take the library functions.
+#include "elementary_tables.inc"
+
+__device__ __forceinline__ double log_fp64(double v) {
+  const uint64_t b = uint64_t(__double_as_longlong(v));
+  if (b - 0x0010000000000000ull >= 0x7fe0000000000000ull) return ::log(v);
+  const int e = int(b >> 52) - 1023;
+  const double m = __longlong_as_double(int64_t((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+  const double tr = fma(m - 1.0, 128.0, 6755399441055744.0);
+  const int j = int(uint64_t(__double_as_longlong(tr)) & 0xffull);
+  const double jd = tr - 6755399441055744.0;
+  const double f = (m - fma(jd, 0.0078125, 1.0)) * __ldg(&kLogInvC[j]);
+  double q = 1.0 / 7.0;
+  q = fma(q, f, -1.0 / 6.0);
+  q = fma(q, f, 0.2);
+  q = fma(q, f, -0.25);
+  q = fma(q, f, 1.0 / 3.0);
+  q = fma(q, f, -0.5);
+  q = fma(q, f, 1.0);
+  const double ed = __longlong_as_double(0x4338000000000000LL + e) - 6755399441055744.0; // double(e)
+  const double hi = fma(ed, kLn2Hi, __ldg(&kLogCHi[j]));
+  const double lo = fma(ed, kLn2Lo, __ldg(&kLogCLo[j])) + q * f;
+  return hi + lo;
+}
+
+__device__ __forceinline__ double exp_fp64(double v) {
+  if ((uint64_t(__double_as_longlong(v)) & 0x7fffffffffffffffull) >= 0x4086200000000000ull) return ::exp(v); // |v| >= 708
+  const double tr = fma(v, k128ByLn2, 6755399441055744.0);
+  const int n = int(__double_as_longlong(tr)); // the low 32 bits: round(128 v / ln 2)
+  const double fn = tr - 6755399441055744.0;
+  double r = fma(-fn, kLn2By128Hi, v);
+  r = fma(-fn, kLn2By128Lo, r);
+  double p = 1.0 / 120.0;
+  p = fma(p, r, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r, 1.0);
+  p *= r;
+  const int k = n & 127;
+  const double th = __ldg(&kExp2Hi[k]);
+  const double res = fma(th, p, __ldg(&kExp2Lo[k])) + th;
+  return __longlong_as_double(__double_as_longlong(res) + (int64_t(n >> 7) << 52));
+}
+
 __device__ __forceinline__ double erfcx_fp64(double a) {
   double r = erfcx_nonneg(fabs(a));
   if (a < 0.0) {
     const double p = a * a, e = fma(a, a, -p); // a^2 = p + e exactly
-    const double ex = 2.0 * exp(p);
+    const double ex = 2.0 * exp_fp64(p);
     r = (p < 709.0) ? fma(ex, e, ex) - r : INFINITY;
   }
   return r;
@@ -103,8 +159,8 @@ template <>
 struct Math<double> {
   static __device__ __forceinline__ double erfcx_(double v) { return erfcx_fp64(v); }
   static __device__ __forceinline__ double erfcx_pos_(double v) { return erfcx_nonneg(v); } // v >= 0
-  static __device__ __forceinline__ double exp_(double v) { return ::exp(v); }
-  static __device__ __forceinline__ double log_(double v) { return ::log(v); }
+  static __device__ __forceinline__ double exp_(double v) { return exp_fp64(v); }
+  static __device__ __forceinline__ double log_(double v) { return log_fp64(v); }
   static __device__ __forceinline__ double sqrt_(double v) { return ::sqrt(v); }
   static __device__ __forceinline__ double cbrt_(double v) { return ::cbrt(v); }
   static __device__ __forceinline__ double ncdf_(double v) { return ::normcdf(v); }
@@ -279,7 +335,7 @@ __device__ __forceinline__ double neg_abs_log_ratio(double mn, double mx, double
   const double r = mn / mx;
   const double c = fma(-r, mx, mn) / mn;
   if (ratio) *ratio = r;
-  return log(r) + c;
+  return log_fp64(r) + c;
 }
 
 // x = -|ln(F/K)|, b_max = e^{x/2} = sqrt(min/max)
@@ -325,9 +381,9 @@ __device__ __forceinline__ Quote classify_quote(double F, double K, double T, do
 // ln beta for a solved row; beta near or below the subnormal range takes it
 // from ln tv so that it keeps its relative accuracy
 __device__ __forceinline__ double log_beta(double beta, double F, double K, double T, double P, int flag) {
-  if (beta > 1e-290) return log(beta);
+  if (beta > 1e-290) return log_fp64(beta);
   const Quote q = classify_quote(F, K, T, P, flag);
-  return log(q.tv) + log(rsqrt(F * K));
+  return log_fp64(q.tv) + log_fp64(rsqrt(F * K));
 }
 
 // ---------------------------------------------------------------------------
@@ -550,25 +606,25 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   last.lbs = lbs;
   // 1/b_s where the middle objective or the larger ratio of the pair needs it
   const bool need_ibs = region == kMidLow || region == kMidHigh || (region == kLower ? hpt > 0.0 : hpt <= 0.0);
-  double ibs = need_ibs ? exp(-lbs) : 0.0;
+  double ibs = need_ibs ? exp_fp64(-lbs) : 0.0;
   double E1 = bmax * ibs;
   double beta_ibs = beta * ibs;
   last.ibs = need_ibs ? ibs : 0.0; // for adjoint_reuse (0: not formed)
   if (!finite64(ibs)) {
     // b_s below ~1e-308 (|ln(F/K)| beyond ~1400): the products in logarithms
-    E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
-    beta_ibs = exp(log(beta) - lbs);
+    E1 = kSqrt2Pi * exp_fp64(0.5 * hpt * hpt);
+    beta_ibs = exp_fp64(log_fp64(beta) - lbs);
     last.ibs = 0.0;
   }
   double nu, L = 0.0, q = 0.0, iL = 0.0;
   if (region == kUpper) {
     const double gam = (hpt > 0.0) ? ya + yb : (E1 - ya) + yb;
     q = 1.0 / gam;
-    nu = -(lnbetac - lbs - log(gam)) * gam;
+    nu = -(lnbetac - lbs - log_fp64(gam)) * gam;
   } else {
     const double rho = taylor ? rho_taylor<double>(h, t) : (hpt <= 0.0 ? ya - yb : (E1 - ya) - yb);
     if (region == kLower) {
-      L = lbs + log(rho); // ln b
+      L = lbs + log_fp64(rho); // ln b
       // 1/rho and 1/L from one division: 1/rho = L / (rho L), 1/L = rho / (rho L)
       const double inv = 1.0 / (rho * L);
       q = L * inv;
@@ -642,7 +698,7 @@ __device__ __forceinline__ double step64_final(double x, double bmax, double bb,
   }
   last.ya = ya;
   last.yb = yb;
-  double ibs = exp(-lbs);
+  double ibs = exp_fp64(-lbs);
   double nu;
   if (finite64(ibs)) {
     const double E1 = bmax * ibs;
@@ -655,13 +711,13 @@ __device__ __forceinline__ double step64_final(double x, double bmax, double bb,
     }
   } else {
     // b_s below the normal range (subnormal beta, or |ln(F/K)| beyond ~1400): in logarithms
-    const double E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
+    const double E1 = kSqrt2Pi * exp_fp64(0.5 * hpt * hpt);
     if (region == kUpper) {
       const double gam = (hpt > 0.0) ? ya + yb : (E1 - ya) + yb;
-      nu = gam - exp(log(bb) - lbs);
+      nu = gam - exp_fp64(log_fp64(bb) - lbs);
     } else {
       const double rho = taylor ? rho_taylor<double>(h, t) : (hpt <= 0.0 ? ya - yb : (E1 - ya) - yb);
-      nu = exp(log(bb) - lbs) - rho;
+      nu = exp_fp64(log_fp64(bb) - lbs) - rho;
     }
     ibs = 0.0; // not usable by the adjoint
   }
@@ -679,7 +735,7 @@ __device__ __forceinline__ double step64_final(double x, double bmax, double bb,
 // The FP64 solve of the binned kernels: guess plus `steps` step64 steps; the
 // last step's Mills ratios are left in `last` for adjoint_reuse.
 __device__ __forceinline__ double solve64(int region, const Node<double>& nd, double lnbeta, int steps, Last& last) {
-  const double lnbetac = (region == kUpper) ? log(nd.bb) : 0.0;
+  const double lnbetac = (region == kUpper) ? log_fp64(nd.bb) : 0.0;
   const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
   double s = region_guess<double>(region, nd, lnbeta);
   for (int i = 0; i < steps; ++i) s = step64<false>(nd.x, nd.bmax, nd.bb, lnbetac, inv_lnbeta, region, s, last);
@@ -859,13 +915,13 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
     const double d = lbs - last.lbs;
     ibs = last.ibs * fma(fma(fma(d, -1.0 / 6.0, 0.5), d, -1.0), d, 1.0);
   } else {
-    ibs = exp(-lbs);
+    ibs = exp_fp64(-lbs);
   }
   double E1 = bmax * ibs, E2 = ibs / bmax;
   if (!finite64(ibs)) {
     // b_s underflows (|ln(F/K)| beyond ~1400): the reflections from their own exponents
-    E1 = kSqrt2Pi * exp(0.5 * hpt * hpt);
-    E2 = kSqrt2Pi * exp(0.5 * zb * zb);
+    E1 = kSqrt2Pi * exp_fp64(0.5 * hpt * hpt);
+    E2 = kSqrt2Pi * exp_fp64(0.5 * zb * zb);
   }
   const double y_hpt = hpt <= 0.0 ? ya : E1 - ya;  // Y(h + t)
   const double y_mhpt = hpt <= 0.0 ? E1 - ya : ya; // Y(-h - t)
@@ -936,8 +992,8 @@ __device__ __forceinline__ Grad gated_adjoint(double F, double K, double T, int 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void bs_factors(double tau, double r, double q, double& er, double& ec) {
   if (isfinite(r) && isfinite(q)) {
-    er = exp(r * tau);
-    ec = exp((r - q) * tau);
+    er = exp_fp64(r * tau);
+    ec = exp_fp64((r - q) * tau);
   } else {
     er = ec = __longlong_as_double(0x7ff8000000000000LL);
   }
