@@ -414,7 +414,7 @@ __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& n
   using M = Math<R>;
   const R ax = -x;
   const R sc = M::sqrt_(R(2) * ax);
-  const R e = M::erfcx_(sc * R(kInvSqrt2));
+  const R e = M::erfcx_pos_(sc * R(kInvSqrt2)); // sc >= 0
   const R bc = R(0.5) * bmax * (R(1) - e);
   const bool low = beta <= bc;
   const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
