@@ -299,6 +299,18 @@ def body_variants(dev, stream, steps):
     for name, mode, rec in (("mixed", 1, mixed), ("learned", 2, learned)):
         run(mode)
         rec["max_rel_sigma_vs_fp64_on_parity_domain"] = float(((sig[dom] - s64[dom]).abs() / s64[dom]).max())
+    # what the network gains over LBR's rational seed: relative error of each seed against the
+    # FP64 root on the first 1M rows
+    m = 1 << 20
+    s_root = s64[:m] * T[:m].sqrt()
+    errs = {}
+    for seed_mode, kw in (("rational", {"mode": "fp64"}), ("mlp", {"mode": "learned", "mlp": trainer})):
+        s0 = pv.iv_guess(F[:m], K[:m], T[:m], P[:m], flag[:m], **kw)
+        good = ok[:m] & torch.isfinite(s0) & (s_root > 0)
+        e = ((s0[good] / s_root[good]) - 1).abs().float()
+        errs[seed_mode] = {f"q{int(q * 1000) / 10:g}": float(torch.quantile(e[: 1 << 20], q))
+                           for q in (0.5, 0.9, 0.99, 0.999)}
+    learned["seed_rel_error_vs_root"] = errs
     del F, K, T, flag, P, sig, st, g, s64, V, dom, trainer
     torch.cuda.empty_cache()
     return {"workload": "body-64M: F=100, ln(K/F)~U[-1,1], T~U[1/365,3], sigma*~U[0.05,1], fwd+bwd",
