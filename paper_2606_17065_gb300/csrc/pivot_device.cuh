@@ -578,7 +578,8 @@ __device__ __forceinline__ R householder_step(R x, R beta, R lnbetac, R inv_lnbe
 // residual, stays double.
 // ---------------------------------------------------------------------------
 struct Last {
-  double za, zb; // arguments of the two Mills ratios at the last evaluation
+  double s;      // the iterate of the last evaluation
+  double za, zb; // arguments of the two Mills ratios there
   double ya, yb; // Y(za), Y(zb)
   double lbs;    // ln b_s there
   double ibs;    // 1/b_s there, or 0 when the step did not form it
@@ -593,6 +594,7 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
   const double lbs = log_bs<double>(h, t);
   const bool taylor = region != kUpper && le_pos(t, kTaylorT) && le_pos(-x, kTaylorX);
+  last.s = s;
   last.za = -fabs(hpt);
   last.zb = h - t;
   last.pair = !taylor;
@@ -688,6 +690,7 @@ __device__ __forceinline__ double step64_final(double x, double bmax, double bb,
   const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
   const double lbs = log_bs<double>(h, t);
   const bool taylor = region != kUpper && le_pos(t, kTaylorT) && le_pos(-x, kTaylorX);
+  last.s = s;
   last.za = -fabs(hpt);
   last.zb = h - t;
   last.pair = !taylor;
@@ -904,8 +907,9 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   const double inv_s = 1.0 / s;
   const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
   const double za = -fabs(hpt), zb = h - t;
-  // the shift is used while it is small (|d| < 1e-4 (1 + |z|): third-order term < 1e-12)
-  const bool near = last.pair && fabs(za - last.za) < 1e-4 * (1.0 - za) && fabs(zb - last.zb) < 1e-4 * (1.0 - zb);
+  // the shift is used while the final step was small: |s - s_last| < 1e-5 s bounds the argument
+  // moves by 1e-5 (|z| + s), so the neglected third-order term stays below ~1e-11 relative
+  const bool near = last.pair && fabs(s - last.s) < 1e-5 * s;
   const double ya = near ? mills_shift(last.ya, last.za, za - last.za) : mills_small(za);
   const double yb = near ? mills_shift(last.yb, last.zb, zb - last.zb) : mills_small(zb);
   const double lbs = log_bs<double>(h, t);
