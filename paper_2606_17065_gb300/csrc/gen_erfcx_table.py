@@ -1,12 +1,24 @@
 """Generate erfcx_table.inc: piecewise polynomial coefficients of erfcx(a) = exp(a^2) erfc(a).
 
-On [0, 16) the function is split into 128 intervals of width 1/8.  On each
-interval it is replaced by its degree-9 Chebyshev interpolant (the polynomial
-through erfcx at the 10 Chebyshev points of the interval), written in the
-monomial basis of tau = 16 (a - a_i) - 1 in [-1, 1].  erfcx is entire, so
-Chebyshev interpolation converges geometrically; at degree 9 the rounded
-coefficients reproduce erfcx to about 1 ulp (checked below against 60-digit
-mpmath).  Beyond 16 the device code uses the asymptotic series instead.
+The range [0, 64) is split into 161 intervals whose index comes from the bit
+pattern of a alone: interval 0 is [0, 1/16); from 1/16 on, each binade
+[2^e, 2^(e+1)), e = -4..5, is split into 16 equal parts, so that interval
+1 + 16 (e + 4) + m (m = the top four mantissa bits of a) is
+[2^e (1 + m/16), 2^e (1 + (m+1)/16)).  The widths grow with a, as erfcx
+flattens (it behaves like 1/(a sqrt pi) far out), and the index needs no
+floating-point instruction.
+
+On each interval erfcx is replaced by its degree-9 Chebyshev interpolant (the
+polynomial through erfcx at the 10 Chebyshev points of the interval), written
+in the monomial basis of tau = a * scale + offset in [-1, 1]; scale = 2 / width
+is a power of two and offset = -(2 a_0 / width + 1) an integer, so tau is
+formed by one fma.  erfcx is entire and, for Re z > 0, close to 1/(z sqrt pi),
+so Chebyshev interpolation converges geometrically on intervals of a fixed
+relative width; at degree 9 the rounded coefficients reproduce erfcx to about
+1 ulp (checked below against 60-digit mpmath).  From 64 on the device code
+uses the asymptotic series.
+
+Each row holds c_0..c_9, scale, offset (12 doubles, 96 bytes).
 
 Run:  python gen_erfcx_table.py   (needs mpmath; writes the .inc next to it)
 """
@@ -14,19 +26,28 @@ import os
 
 import mpmath as mp
 
-WIDTH = mp.mpf(1) / 8
-N_INT = 128
 DEG = 9
+SUB = 16          # parts per binade
+E_MIN, E_MAX = -4, 5  # binades [2^e, 2^(e+1)) covered by the split
+
+
+def intervals():
+    out = [(mp.mpf(0), mp.mpf(1) / 16)]
+    for e in range(E_MIN, E_MAX + 1):
+        for m in range(SUB):
+            w = mp.mpf(2) ** e / SUB
+            a0 = mp.mpf(2) ** e + m * w
+            out.append((a0, a0 + w))
+    return out
 
 
 def erfcx(a):
     return mp.erfc(a) * mp.exp(a * a)
 
 
-def interval_coefficients(i):
-    a0 = i * WIDTH
+def interval_coefficients(a0, w):
     nodes = [mp.cos(mp.pi * (j + mp.mpf(1) / 2) / (DEG + 1)) for j in range(DEG + 1)]
-    vals = [erfcx(a0 + WIDTH * (t + 1) / 2) for t in nodes]
+    vals = [erfcx(a0 + w * (t + 1) / 2) for t in nodes]
     A = mp.matrix([[t ** k for k in range(DEG + 1)] for t in nodes])
     c = mp.lu_solve(A, mp.matrix(vals))
     return [c[k] for k in range(DEG + 1)]
@@ -36,27 +57,30 @@ def main():
     mp.mp.dps = 60
     rows = []
     worst = 0.0
-    for i in range(N_INT):
-        c = interval_coefficients(i)
-        cd = [float(x) for x in c]
-        rows.append(cd)
+    for a0, a1 in intervals():
+        w = a1 - a0
+        cd = [float(x) for x in interval_coefficients(a0, w)]
+        scale, offset = float(2 / w), float(-(2 * a0 / w + 1))
+        assert scale == 2 / w and offset == -(2 * a0 / w + 1)  # both exact in double
+        rows.append(cd + [scale, offset])
         for j in range(33):
             t = -1 + mp.mpf(2) * j / 32
             v = 0.0
             for k in range(DEG, -1, -1):
                 v = v * float(t) + cd[k]
-            ref = erfcx(i * WIDTH + WIDTH * (t + 1) / 2)
+            ref = erfcx(a0 + w * (t + 1) / 2)
             worst = max(worst, float(abs(v - ref) / ref))
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "erfcx_table.inc")
     with open(out, "w") as fh:
-        fh.write("// Generated by gen_erfcx_table.py: degree-9 Chebyshev interpolants of\n")
-        fh.write("// erfcx(a) on [i/8, (i+1)/8), i = 0..127, monomial coefficients in\n")
-        fh.write(f"// tau = 16 (a - i/8) - 1.  Max relative error in double: {worst:.3e}.\n")
-        fh.write(f"static __device__ const double kErfcxCoef[{N_INT}][{DEG + 1}] = {{\n")
+        fh.write("// Generated by gen_erfcx_table.py: degree-9 Chebyshev interpolants of erfcx(a)\n")
+        fh.write("// on [0, 1/16) and on 16 equal parts of each binade [2^e, 2^(e+1)), e = -4..5.\n")
+        fh.write("// Row: monomial coefficients c_0..c_9 in tau = a * scale + offset, then scale, offset.\n")
+        fh.write(f"// Max relative error in double: {worst:.3e}.\n")
+        fh.write(f"static __device__ const double kErfcxCoef[{len(rows)}][{DEG + 3}] = {{\n")
         for cd in rows:
             fh.write("    {" + ", ".join(repr(x) for x in cd) + "},\n")
         fh.write("};\n")
-    print(f"wrote {out}; max relative error {worst:.3e}")
+    print(f"wrote {out}; {len(rows)} intervals; max relative error {worst:.3e}")
 
 
 if __name__ == "__main__":

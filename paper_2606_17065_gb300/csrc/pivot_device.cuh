@@ -50,28 +50,28 @@ enum Region : int { kLower = 0, kMidLow = 1, kMidHigh = 2, kUpper = 3 };
 template <typename R>
 struct Math;
 // erfcx(a) = exp(a^2) erfc(a) in FP64 for the Mills ratios: degree-9
-// Chebyshev interpolants on 128 intervals of [0, 16) (coefficients written by
+// Chebyshev interpolants on 161 intervals of [0, 64) (coefficients written by
 // gen_erfcx_table.py, ~1 ulp), the asymptotic series
-// erfcx(a) ~ (1/(a sqrt pi)) sum_n (-1)^n (2n-1)!! / (2a^2)^n beyond 16 (ten
-// terms, truncation < 1e-18 there), and erfcx(a) = 2 exp(a^2) - erfcx(-a) for
-// a < 0 with a^2 split exactly by an fma.  About a third of the FP64 work of
-// a general-purpose erfcx: one conversion, one fma chain and table loads
-// that hit L1.
+// erfcx(a) ~ (1/(a sqrt pi)) sum_n (-1)^n (2n-1)!! / (2a^2)^n from 64 on (ten
+// terms, truncation < 1e-30 there), and erfcx(a) = 2 exp(a^2) - erfcx(-a) for
+// a < 0 with a^2 split exactly by an fma.  The interval is read off the bit
+// pattern of a (interval 0 = [0, 1/16), then 16 equal parts per binade up to
+// 64), so the table covers every Mills ratio of a normal-range price in one
+// branch (the series only serves iterates far outside it) and the FP64 pipe
+// sees one fma for the local variable and the Horner chain; the table rows are
+// 96 bytes and hit L1.
 #include "erfcx_table.inc"
 
 __device__ __forceinline__ double erfcx_nonneg(double a) {
-  if ((uint64_t(__double_as_longlong(a)) & 0x7fffffffffffffffull) < 0x4030000000000000ull) { // |a| < 16 (a = -0 too)
-    // interval k = floor(8a) from the rounding of (8a - 1/2) + 1.5 2^52 (ulp 1 there; 8a - 1/2
-    // is exact): k sits in the low mantissa bits, so neither a floor nor a conversion runs on
-    // the FP64 pipe (an exact 8a = k + 1 may land on k with tau = 1, the interval's end)
-    const double tr = fma(a, 8.0, -0.5) + 6755399441055744.0;
-    const int k = int(uint64_t(__double_as_longlong(tr)) & 127ull);
-    const double fi = tr - 6755399441055744.0;
+  const uint64_t bits = uint64_t(__double_as_longlong(a)) & 0x7fffffffffffffffull; // a = -0 too
+  if (bits < 0x4050000000000000ull) { // |a| < 64
+    // biased exponent and top four mantissa bits, less those of 1/16, plus one (0 below 1/16)
+    const int k = max(int(bits >> 48) - ((1023 - 4) << 4) + 1, 0);
     const double* c = kErfcxCoef[k];
-    const double tau = fma(a - fi * 0.125, 16.0, -1.0);
+    const double tau = fma(a, __ldg(c + 10), __ldg(c + 11)); // in [-1, 1]; scale 2^j, offset an integer
     double v = __ldg(c + 9);
 #pragma unroll
-    for (int k = 8; k >= 0; --k) v = fma(v, tau, __ldg(c + k));
+    for (int j = 8; j >= 0; --j) v = fma(v, tau, __ldg(c + j));
     return v;
   }
   const double ia = 1.0 / a;
