@@ -137,18 +137,19 @@ struct TileCfg {
   // six node fields per row (+ e^{r tau}, e^{(r-q) tau} in the Black-Scholes form), two row lists
   static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
 };
-// Region bins.  FP64 form: the 4 regions, plus 2 bins for middle-region rows
-// near the money (|x| <= kTaylorX), the only rows whose b may take the
-// Taylor series of rho: kept apart, a warp runs one of the two forms of rho;
-// and bin 6 for lower-region rows with beta below kDeepBeta, whose Mills
-// ratios (|h -+ t| beyond ~20 at ln beta ~ -h^2/2) take erfcx's asymptotic
-// series rather than its table.
+// Region bins.  FP64 form: the 4 regions, plus bins 4, 5 for middle-region
+// rows and bin 7 for lower-region rows near the money (|x| <= kTaylorX), the
+// only rows whose b may take the Taylor series of rho: kept apart, a warp runs
+// one of the two forms of rho (and, in the adjoint, one form of the Mills
+// ratios); and bin 6 for lower-region rows with beta below kDeepBeta, whose
+// guess takes the scaled cube root and, below ~1e-290, ln beta from the
+// row's time value.
 // Mixed form: 4 float-seeded region bins, 4 FP64 bins for rows outside the
 // float range (b_max - beta below kMixedFloor, |x| above kMixedMaxAbsX, or
 // beta below kMixedFloor near the money), bin kDeepBin (lower-tail rows with
 // beta below kMixedFloor and |x| >= kDeepMinAbsX, seeded in float from
-// ln beta), and 2 near-the-money float bins.
-constexpr int kMaxBins = 11;
+// ln beta), and 3 near-the-money float bins (middle 9, 10; lower 11).
+constexpr int kMaxBins = 12;
 constexpr int kDeepBin = 8;
 constexpr double kDeepBeta = 1e-100;
 constexpr double kMixedFloor = 1e-30;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
   uint16_t* s_list = reinterpret_cast<uint16_t*>(s_ec + (kBS ? kTile : 0));  // phase 1 -> 2: rows to solve
   uint16_t* s_order = s_list + kTile;                                        // phase 2 -> 3: region order
   __shared__ int s_nsolve;
-  constexpr int kBins = kMixed ? 11 : 7;
+  constexpr int kBins = kMixed ? 12 : 8;
   __shared__ int s_cnt[kMaxBins];
   __shared__ int s_off[kMaxBins + 1];
 
@@ -290,12 +291,15 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
           s_bsn[r] = nd.bsn;
           s_bb[r] = nd.bb;
         }
-        // middle rows near the money to their own bins (FP64 form: 1, 2 -> 4, 5; mixed float: 1, 2 -> 9, 10)
+        // lower and middle rows near the money to their own bins (FP64 form: 0, 1, 2 -> 7, 4, 5;
+        // mixed float: 0, 1, 2 -> 11, 9, 10)
         if (x >= -pivot::kTaylorX) {
           if (!kMixed && (rg == pivot::kMidLow || rg == pivot::kMidHigh)) rg += 3;
+          else if (!kMixed && rg == pivot::kLower) rg = 7;
           if (kMixed && !fp64_row && (rg == pivot::kMidLow || rg == pivot::kMidHigh)) rg += 8;
+          else if (kMixed && !fp64_row && rg == pivot::kLower) rg = 11;
         }
-        if (!kMixed && rg == pivot::kLower && beta < kDeepBeta) rg = 6;
+        if (!kMixed && (rg == pivot::kLower || rg == 7) && beta < kDeepBeta) rg = 6;
         row[j] = r;
       }
       reg[j] = rg;
@@ -329,8 +333,8 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
       row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
       const int fl = a.flag[i];
       const bool deep = kMixed && bin == kDeepBin;
-      const int rg = kMixed ? (deep ? int(pivot::kLower) : bin > kDeepBin ? bin - 8 : (bin & 3))
-                            : (bin < 4 ? bin : bin == 6 ? int(pivot::kLower) : bin - 3);
+      const int rg = kMixed ? (deep || bin == 11 ? int(pivot::kLower) : bin > kDeepBin ? bin - 8 : (bin & 3))
+                            : (bin < 4 ? bin : bin >= 6 ? int(pivot::kLower) : bin - 3);
       const bool float_row = kMixed && (bin < 4 || bin >= kDeepBin);
       const double bb = s_bb[r];
       // ln beta for the FP64 solve of a lower-region row (the float-seeded rows of the mixed form do without)
