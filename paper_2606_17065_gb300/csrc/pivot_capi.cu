@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kBlock) k_elementary(int fn, int64_t n, const 
                                                         double* __restrict__ y) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
-    y[i] = fn == 0 ? pivot::log_fp64(x[i]) : pivot::exp_fp64(x[i]);
+    y[i] = fn == 0 ? pivot::log_fp64(x[i]) : fn == 1 ? pivot::exp_fp64(x[i]) : pivot::neg_ncdfinv<double>(x[i], true);
 }
 
 __global__ void __launch_bounds__(kBlock) k_mills_ratio(int64_t n, const double* __restrict__ z,
@@ -151,7 +151,6 @@ struct TileCfg {
 // ln beta), and 3 near-the-money float bins (middle 9, 10; lower 11).
 constexpr int kMaxBins = 12;
 constexpr int kDeepBin = 8;
-constexpr double kDeepBeta = 1e-100;
 constexpr double kMixedFloor = 1e-30;
 constexpr double kMixedMaxAbsX = 80.0;
 constexpr double kDeepMinAbsX = 0.1;
@@ -299,7 +298,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
           if (kMixed && !fp64_row && (rg == pivot::kMidLow || rg == pivot::kMidHigh)) rg += 8;
           else if (kMixed && !fp64_row && rg == pivot::kLower) rg = 11;
         }
-        if (!kMixed && (rg == pivot::kLower || rg == 7) && beta < kDeepBeta) rg = 6;
+        if (!kMixed && (rg == pivot::kLower || rg == 7) && beta < pivot::kDeepBeta) rg = 6;
         row[j] = r;
       }
       reg[j] = rg;
@@ -337,55 +336,50 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
                             : (bin < 4 ? bin : bin >= 6 ? int(pivot::kLower) : bin - 3);
       const bool float_row = kMixed && (bin < 4 || bin >= kDeepBin);
       const double bb = s_bb[r];
-      // ln beta for the FP64 solve of a lower-region row (the float-seeded rows of the mixed form do without)
-      const double lnbeta = (rg == pivot::kLower && !float_row) ? pivot::log_beta(bb, F, K, T, P, fl) : 0.0;
       double s = 0.0;
       pivot::Last last;
-      if (deep) {
-        s = pivot::solve_deep_mixed64(s_x[r], s_bmax[r], bb, last);
-        if (!pivot::pos_finite(s)) {
-          // not accepted: the FP64 path from the row's inputs
-          const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
-          double x, bmax;
-          pivot::moneyness(F, K, x, bmax);
-          const double rsq = rsqrt(F * K);
-          pivot::Node<double> nd;
-          const int rg2 = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
-          const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, P, fl) : 0.0;
-          s = pivot::solve64(rg2, nd, lnb2, a.steps, last);
+      // FP64 bins, and float-seeded rows whose float solve was not accepted, meet at one FP64 solve
+      bool fp64 = !float_row;
+      if (float_row) {
+        if (deep) {
+          s = pivot::solve_deep_mixed64(s_x[r], s_bmax[r], bb, last);
+        } else {
+          pivot::Node<float> nf;
+          const float2 p0 = *reinterpret_cast<const float2*>(&s_e[r]);
+          const float2 p1 = *reinterpret_cast<const float2*>(&s_bn[r]);
+          const float2 p2 = *reinterpret_cast<const float2*>(&s_bsn[r]);
+          nf.e = p0.x;
+          nf.bn = p0.y;
+          nf.bsn = p1.x;
+          nf.x = p1.y;
+          nf.bmax = p2.x;
+          nf.bb = p2.y;
+          s = pivot::solve_mixed64(rg, nf, s_x[r], s_bmax[r], bb, a.steps, last);
         }
-      } else if (float_row) {
-        pivot::Node<float> nf;
-        const float2 p0 = *reinterpret_cast<const float2*>(&s_e[r]);
-        const float2 p1 = *reinterpret_cast<const float2*>(&s_bn[r]);
-        const float2 p2 = *reinterpret_cast<const float2*>(&s_bsn[r]);
-        nf.e = p0.x;
-        nf.bn = p0.y;
-        nf.bsn = p1.x;
-        nf.x = p1.y;
-        nf.bmax = p2.x;
-        nf.bb = p2.y;
-        s = pivot::solve_mixed64(rg, nf, s_x[r], s_bmax[r], bb, a.steps, last);
-        if (!pivot::pos_finite(s)) {
-          // float seed failed: redo the row in double from its inputs
-          const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
-          double x, bmax;
-          pivot::moneyness(F, K, x, bmax);
-          const double rsq = rsqrt(F * K);
-          pivot::Node<double> nd;
-          const int rg2 = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
-          const double lnb2 = (rg2 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, P, fl) : 0.0;
-          s = pivot::solve64(rg2, nd, lnb2, a.steps, last);
-        }
-      } else {
+        fp64 = !pivot::pos_finite(s);
+      }
+      if (fp64) {
         pivot::Node<double> nd;
-        nd.x = s_x[r];
-        nd.bmax = s_bmax[r];
-        nd.e = s_e[r];
-        nd.bn = s_bn[r];
-        nd.bsn = s_bsn[r];
-        nd.bb = bb;
-        s = pivot::solve64(rg, nd, lnbeta, a.steps, last);
+        int rg64 = rg;
+        if (float_row) {
+          // not accepted: the FP64 node from the row's inputs (its shared slots hold the float node)
+          const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
+          double x, bmax;
+          pivot::moneyness(F, K, x, bmax);
+          const double rsq = rsqrt(F * K);
+          rg64 = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
+        } else {
+          nd.x = s_x[r];
+          nd.bmax = s_bmax[r];
+          nd.e = s_e[r];
+          nd.bn = s_bn[r];
+          nd.bsn = s_bsn[r];
+          nd.bb = bb;
+        }
+        // ln beta for the lower region's objective
+        const double lnbeta = (rg64 == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, P, fl) : 0.0;
+        // (the mixed form's FP64 rows lie mostly below the float range: the library's Phi^{-1})
+        s = pivot::solve64<!kMixed>(rg64, nd, lnbeta, a.steps, last);
       }
       const double inv_sqT = rsqrt(T);
       const double sig = s * inv_sqT;
@@ -675,7 +669,7 @@ int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream) {
 }
 
 int pivot_elementary(int32_t fn, int64_t n, const double* x, double* y, void* stream) {
-  if (fn != 0 && fn != 1) return PIVOT_E_OPTS;
+  if (fn < 0 || fn > 2) return PIVOT_E_OPTS;
   if (n < 0) return PIVOT_E_SIZE;
   if (n == 0) return PIVOT_OK;
   int dev = -1;

@@ -164,7 +164,6 @@ struct Math<double> {
   static __device__ __forceinline__ double sqrt_(double v) { return ::sqrt(v); }
   static __device__ __forceinline__ double cbrt_(double v) { return ::cbrt(v); }
   static __device__ __forceinline__ double ncdf_(double v) { return ::normcdf(v); }
-  static __device__ __forceinline__ double ncdfinv_(double v) { return ::normcdfinv(v); }
   static __device__ __forceinline__ double fma_(double a, double b, double c) { return ::fma(a, b, c); }
   static __device__ __forceinline__ double fmin_(double a, double b) { return ::fmin(a, b); }
   static __device__ __forceinline__ double fmax_(double a, double b) { return ::fmax(a, b); }
@@ -181,7 +180,6 @@ struct Math<float> {
   static __device__ __forceinline__ float sqrt_(float v) { return ::sqrtf(v); }
   static __device__ __forceinline__ float cbrt_(float v) { return ::cbrtf(v); }
   static __device__ __forceinline__ float ncdf_(float v) { return ::normcdff(v); }
-  static __device__ __forceinline__ float ncdfinv_(float v) { return ::normcdfinvf(v); }
   static __device__ __forceinline__ float fma_(float a, float b, float c) { return ::fmaf(a, b, c); }
   static __device__ __forceinline__ float fmin_(float a, float b) { return ::fminf(a, b); }
   static __device__ __forceinline__ float fmax_(float a, float b) { return ::fmaxf(a, b); }
@@ -439,9 +437,36 @@ __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& n
   return region;
 }
 
+// -Phi^{-1}(G) for the guesses, G in (0, 1/2].  In double, for G from 1e-37
+// on (the float range) and where `fast` (rows with beta >= kDeepBeta, whose
+// lower-region G stays above ~1e-35): a float start, within a few float ulps,
+// and one Newton step on Phi(y) = G in double,
+//   y1 = y0 - (Phi(y0) - G)/phi(y0) = y0 - (Y(y0) - sqrt(2 pi) G e^{y0^2/2}),
+// whose error ~ |y0| e0^2 / 2 (e0 ~ 1e-6 at y0 ~ -13) is below 1e-10; near
+// y = 0 the rounding of the difference leaves ~3e-16 absolute.  Both are far
+// below the guess's own interpolation error.  It runs on the table-driven erfcx and exp
+// rather than the general-purpose FP64 normcdfinv and its branches.  Other
+// arguments take the library function.
+constexpr double kDeepBeta = 1e-100;
+template <typename R>
+__device__ __forceinline__ R neg_ncdfinv(R G, bool fast);
+template <>
+__device__ __forceinline__ float neg_ncdfinv<float>(float G, bool) { return -::normcdfinvf(G); }
+template <>
+__device__ __forceinline__ double neg_ncdfinv<double>(double G, bool fast) {
+  if (fast && G >= 1e-37) {
+    const double y0 = double(::normcdfinvf(float(G))); // <= 0
+    const double ey = exp_fp64(0.5 * y0 * y0);         // e^{y0^2/2} = 1 / (sqrt(2 pi) phi(y0))
+    return -(fma(kSqrt2Pi * G, ey, -(kSqrtPiOver2 * erfcx_nonneg(-y0 * kInvSqrt2))) + y0);
+  }
+  return -::normcdfinv(G);
+}
+
 // Rational initial guess s^(0) of the row's region from its node.
 // lnbeta is ln beta (lower region only).
-template <typename R>
+// kFastInv: -Phi^{-1} by neg_ncdfinv's float start and Newton step where it applies (else the
+// library function throughout)
+template <typename R, bool kFastInv = true>
 __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbeta) {
   using M = Math<R>;
   const R x = nd.x, ax = -x;
@@ -469,7 +494,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R dGl = R(3) * bl * (R(kInvSqrt2Pi) * eal) * al / (sl * ul * bsl);
       const R r = shape_monotone<R>(ul, R(0), Gl, R(1), dGl);
       const R G = M::fmin_(rational_cubic<R>(u, R(0), ul, R(0), Gl, R(1), dGl, r), R(0.5));
-      return ax * R(kInvSqrt3) / (-M::ncdfinv_(G));
+      return ax * R(kInvSqrt3) / neg_ncdfinv<R>(G, kFastInv && beta >= R(kDeepBeta));
     }
     case kMidLow: {
       // rational cubic in b on [b_l, b_c], zero curvature of s(b) at the inflection b_c
@@ -505,7 +530,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R dvu = (R(kInvSqrt2Pi) * esu) / nd.bsn;
       const R r = shape_monotone<R>(uu, R(0), vu, R(1), dvu);
       const R v = M::fmin_(rational_cubic<R>(R(0.5) * nd.bb, R(0), uu, R(0), vu, R(1), dvu, r), R(0.5));
-      return R(-2) * M::ncdfinv_(v);
+      return R(2) * neg_ncdfinv<R>(v, kFastInv);
     }
   }
 }
@@ -737,10 +762,11 @@ __device__ __forceinline__ double step64_final(double x, double bmax, double bb,
 
 // The FP64 solve of the binned kernels: guess plus `steps` step64 steps; the
 // last step's Mills ratios are left in `last` for adjoint_reuse.
+template <bool kFastInv = true>
 __device__ __forceinline__ double solve64(int region, const Node<double>& nd, double lnbeta, int steps, Last& last) {
   const double lnbetac = (region == kUpper) ? log_fp64(nd.bb) : 0.0;
   const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
-  double s = region_guess<double>(region, nd, lnbeta);
+  double s = region_guess<double, kFastInv>(region, nd, lnbeta);
   for (int i = 0; i < steps; ++i) s = step64<false>(nd.x, nd.bmax, nd.bb, lnbetac, inv_lnbeta, region, s, last);
   return s;
 }

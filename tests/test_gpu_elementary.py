@@ -1,5 +1,6 @@
 """The device FP64 log and exp (table-driven, used by the solver) against numpy's: within
-2 ulp on wide ranges, near 1 for the logarithm, and IEEE special values."""
+2 ulp on wide ranges, near 1 for the logarithm, and IEEE special values; and the guesses'
+-Phi^{-1} against mpmath."""
 import numpy as np
 import pytest
 
@@ -49,3 +50,30 @@ def test_exp_fp64():
     # beyond |v| = 708 the library exponential answers; in the subnormal range it may round
     # differently from the host's by a few units of the smallest subnormal
     assert np.allclose(got[m], ref[m], rtol=4e-16, atol=1e-322)
+
+
+def test_neg_ncdfinv_of_the_guesses():
+    """-Phi^{-1}(G) of the lower- and upper-region guesses: a float start and one FP64 Newton step
+    from 1e-37 on, the library's normcdfinv below; against 50-digit mpmath and scipy's ndtri."""
+    mp = pytest.importorskip("mpmath")
+    special = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(3)
+    G = np.concatenate([np.logspace(-300, np.log10(0.5), 400), np.logspace(-37, np.log10(0.5), 600),
+                        [0.5, np.nextafter(0.5, 0), 0.49999, 1e-37, np.nextafter(1e-37, 0)]])
+    got = to_np(api.elementary("neg_ncdfinv", to_dev(G)))
+    with mp.workdps(50):
+        # the root of erfc(y / sqrt 2) / 2 = G (no cancellation in the tail), from scipy's value
+        ref = np.array([float(mp.findroot(lambda y: mp.erfc(y / mp.sqrt(2)) / 2 - mp.mpf(float(g)), -special.ndtri(g)))
+                        for g in G])
+    err = np.abs(got - ref)
+    # Newton from a float start: ~1e-11 relative; near G = 1/2 (y -> 0) ~3e-16 absolute
+    assert np.all(err <= 1e-10 * np.abs(ref) + 1e-15), (err / np.maximum(np.abs(ref), 1e-300)).max()
+    # the library branch below 1e-37 is FP64-accurate
+    lo = G < 1e-37
+    assert np.all(err[lo] <= 1e-14 * np.abs(ref[lo]))
+    assert got[G == 0.5][0] == 0.0 or abs(got[G == 0.5][0]) < 1e-15
+    # dense sample against scipy
+    g2 = np.exp(rng.uniform(np.log(1e-37), np.log(0.5), 200_000))
+    got2 = to_np(api.elementary("neg_ncdfinv", to_dev(g2)))
+    ref2 = -special.ndtri(g2)
+    assert np.all(np.abs(got2 - ref2) <= 1e-10 * np.abs(ref2) + 1e-15)
