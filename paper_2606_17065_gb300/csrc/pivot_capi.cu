@@ -120,23 +120,14 @@ __global__ void __launch_bounds__(kBlock) k_bs_iv_backward(Args a) {
 //           and region of each row, kept in shared memory, counted per region.
 //  phase 3: the rows are laid out region after region and consumed in that
 //           order, so a warp runs one region's guess and Householder
-//           objective with all of its lanes; only warps straddling a region
-//           boundary diverge.  sigma and the gated adjoint are written here.
+//           objective with all of its lanes.  Each bin is consumed in whole
+//           warps: its last, partial warp of rows (with their nodes) is carried
+//           to the block's next tile and joins that tile's bin in front, so
+//           that no warp runs with idle lanes or two regions' code, except in
+//           the block's last tile, which takes every row.  sigma and the gated
+//           adjoint are written here.
 // The grid is persistent: blocks stride over tiles.
 // ---------------------------------------------------------------------------
-// Tile rows per block: 2,048 for the Black-76 forms (2 blocks of 256 threads
-// per SM, 106,496 B of shared memory each), 1,536 for the Black-Scholes form,
-// whose two extra doubles per row would not let two 2,048-row blocks fit
-// (2 blocks of 104,448 B).  Larger tiles pack the region bins of phase 3 into
-// fewer partially filled warps; 2 blocks per SM leave ~128 registers a thread.
-template <bool kBS>
-struct TileCfg {
-  static constexpr int kTile = kBS ? 1536 : 2048;
-  static constexpr int kMinBlocks = 2;
-  static constexpr int kRowsPerThread = kTile / kBlock;
-  // six node fields per row (+ e^{r tau}, e^{(r-q) tau} in the Black-Scholes form), two row lists
-  static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kTile * sizeof(double) + 2 * kTile * sizeof(uint16_t);
-};
 // Region bins.  FP64 form: the 4 regions, plus bins 4, 5 for middle-region
 // rows and bin 7 for lower-region rows near the money (|x| <= kTaylorX), the
 // only rows whose b may take the Taylor series of rho: kept apart, a warp runs
@@ -150,6 +141,29 @@ struct TileCfg {
 // beta below kMixedFloor and |x| >= kDeepMinAbsX, seeded in float from
 // ln beta), and 3 near-the-money float bins (middle 9, 10; lower 11).
 constexpr int kMaxBins = 12;
+// Rows a bin may carry from one tile to the next (its last, partial warp).
+constexpr int kCarryPerBin = 31;
+
+// Shared memory of the binned kernel, in row slots: kCarry slots hold the
+// rows carried over from earlier tiles (bin b in [31 b, 31 b + 31)), then
+// kTile slots the current tile's rows.  Per slot: six node fields (+ e^{r tau},
+// e^{(r-q) tau} in the Black-Scholes form) and the phase-3 order (whose first
+// kTile entries also serve as the phase 1 -> 2 list); per carry slot: the
+// row's global index and a move record.  Tiles: 1,792 rows for the FP64
+// Black-76 form, 1,536 for its mixed form (12 bins), 1,280 / 1,024 for the
+// Black-Scholes forms, so that 2 blocks of 256 threads fit an SM (~128
+// registers a thread).
+template <bool kBS, bool kMixed>
+struct TileCfg {
+  static constexpr int kBins = kMixed ? 12 : 8;
+  static constexpr int kCarry = kCarryPerBin * kBins;
+  static constexpr int kTile = kBS ? (kMixed ? 1024 : 1280) : (kMixed ? 1536 : 1792);
+  static constexpr int kMinBlocks = 2;
+  static constexpr int kRowsPerThread = kTile / kBlock;
+  static constexpr int kSlots = kCarry + kTile;
+  static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kSlots * sizeof(double) + size_t(kCarry) * sizeof(int64_t) +
+                                  size_t(kSlots) * sizeof(uint16_t) + 2 * size_t(kCarry) * sizeof(uint16_t);
+};
 constexpr int kDeepBin = 8;
 constexpr double kMixedFloor = 1e-30;
 constexpr double kMixedMaxAbsX = 80.0;
@@ -172,23 +186,31 @@ __device__ __forceinline__ void row_fp(const Args& a, int64_t i, int r, const do
 }
 
 template <bool kBackward, bool kMixed, bool kBS>
-__global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(Args a) {
-  constexpr int kTile = TileCfg<kBS>::kTile;
-  constexpr int kRowsPerThread = TileCfg<kBS>::kRowsPerThread;
+__global__ void __launch_bounds__(kBlock, TileCfg<kBS, kMixed>::kMinBlocks) k_iv_binned(Args a) {
+  using Cfg = TileCfg<kBS, kMixed>;
+  constexpr int kRowsPerThread = Cfg::kRowsPerThread;
+  constexpr int kBins = Cfg::kBins;
+  constexpr int kCarry = Cfg::kCarry;
+  constexpr int kSlots = Cfg::kSlots;
+  // per row slot (carry slots first, then the tile's): its node, in structure-of-arrays form
   extern __shared__ double smem[];
   double* s_x = smem;
-  double* s_bmax = s_x + kTile;
-  double* s_e = s_bmax + kTile;
-  double* s_bn = s_e + kTile;
-  double* s_bsn = s_bn + kTile;
-  double* s_bb = s_bsn + kTile;
-  double* s_er = s_bb + kTile;                     // kBS only
-  double* s_ec = s_er + (kBS ? kTile : 0);          // kBS only
-  uint16_t* s_list = reinterpret_cast<uint16_t*>(s_ec + (kBS ? kTile : 0));  // phase 1 -> 2: rows to solve
-  uint16_t* s_order = s_list + kTile;                                        // phase 2 -> 3: region order
-  __shared__ int s_nsolve;
-  constexpr int kBins = kMixed ? 12 : 8;
-  __shared__ int s_cnt[kMaxBins];
+  double* s_bmax = s_x + kSlots;
+  double* s_e = s_bmax + kSlots;
+  double* s_bn = s_e + kSlots;
+  double* s_bsn = s_bn + kSlots;
+  double* s_bb = s_bsn + kSlots;
+  double* s_er = s_bb + kSlots;                      // kBS only
+  double* s_ec = s_er + (kBS ? kSlots : 0);          // kBS only
+  int64_t* s_gidx = reinterpret_cast<int64_t*>(s_ec + (kBS ? kSlots : 0));  // global row of a carry slot
+  uint16_t* s_order = reinterpret_cast<uint16_t*>(s_gidx + kCarry);         // phase 2 -> 3: slots in bin order
+  uint16_t* s_list = s_order;   // phase 1 -> 2: slots to solve (read into registers before the order is written)
+  uint16_t* s_mv_src = s_order + kSlots;                                     // leftover rows: tile slot ...
+  uint16_t* s_mv_dst = s_mv_src + kCarry;                                    // ... -> carry slot
+  __shared__ int s_nsolve, s_nmv;
+  __shared__ int s_cnt[kMaxBins];   // rows per bin, carried ones included
+  __shared__ int s_full[kMaxBins];  // rows per bin consumed by this tile
+  __shared__ int s_ccnt[kMaxBins];  // rows per bin carried into the next tile
   __shared__ int s_off[kMaxBins + 1];
 
   const int tid = threadIdx.x;
@@ -197,15 +219,20 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
   // every SM gets work; the shared arrays keep their kTile strides
   const int tile = a.tile;
   const int jmax = tile / kBlock;
+  if (tid < kBins) s_ccnt[tid] = 0;
   for (int64_t base = int64_t(blockIdx.x) * tile; base < a.n; base += int64_t(gridDim.x) * tile) {
-    if (tid < kBins) s_cnt[tid] = 0;
-    if (tid == 0) s_nsolve = 0;
+    const bool last = base + int64_t(gridDim.x) * tile >= a.n;  // the block's last tile takes every row
+    if (tid < kBins) s_cnt[tid] = s_ccnt[tid];  // carried rows come first in their bins
+    if (tid == 0) {
+      s_nsolve = 0;
+      s_nmv = 0;
+    }
     __syncthreads();
     // ---- phase 1
 #pragma unroll
     for (int j = 0; j < kRowsPerThread; ++j) {
-      const int r = j * kBlock + tid;
-      const int64_t i = base + r;
+      const int r = kCarry + j * kBlock + tid;  // slot
+      const int64_t i = base + (j * kBlock + tid);
       bool solve = false;
       if (j < jmax && i < a.n) {
         const double K = a.K[i], T = a.T[i];
@@ -247,7 +274,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
       row[j] = 0;
       if (qi < nsolve) {
         const int r = s_list[qi];
-        const int64_t i = base + r;
+        const int64_t i = base + (r - kCarry);
         const double K = a.K[i];
         const double F = kBS ? a.F[i] * s_ec[r] : a.F[i];
         double x, bmax;
@@ -312,21 +339,42 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
     __syncthreads();
     if (tid == 0) {
       s_off[0] = 0;
-      for (int k = 0; k < kBins; ++k) s_off[k + 1] = s_off[k] + s_cnt[k];
+      for (int k = 0; k < kBins; ++k) {
+        const int full = last ? s_cnt[k] : (s_cnt[k] & ~31);
+        s_full[k] = full;
+        s_off[k + 1] = s_off[k] + full;
+      }
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kRowsPerThread; ++j)
-      if (reg[j] >= 0) s_order[s_off[reg[j]] + pos[j]] = uint16_t(row[j]);
+    for (int j = 0; j < kRowsPerThread; ++j) {
+      const int b = reg[j];
+      if (b >= 0) {
+        const int p = pos[j], full = s_full[b];
+        if (p < full) {
+          s_order[s_off[b] + p] = uint16_t(row[j]);
+        } else {
+          // the bin's partial warp: to carry slot p - full of the bin (p - full <= 30)
+          const int m = atomicAdd(&s_nmv, 1);
+          s_mv_src[m] = uint16_t(row[j]);
+          s_mv_dst[m] = uint16_t(kCarryPerBin * b + p - full);
+        }
+      }
+    }
+    // carried rows hold the first positions of their bins; those not consumed stay in place
+    for (int c = tid; c < kCarry; c += kBlock) {
+      const int b = c / kCarryPerBin, p = c - b * kCarryPerBin;
+      if (p < s_ccnt[b] && p < s_full[b]) s_order[s_off[b] + p] = uint16_t(c);
+    }
     __syncthreads();
     // ---- phase 3
     const int total = s_off[kBins];
     for (int qi = tid; qi < total; qi += kBlock) {
-      const int r = s_order[qi];
+      const int r = s_order[qi];  // slot
       int bin = 0;
 #pragma unroll
       for (int k = 1; k < kBins; ++k) bin += (qi >= s_off[k]) ? 1 : 0;
-      const int64_t i = base + r;
+      const int64_t i = r < kCarry ? s_gidx[r] : base + (r - kCarry);
       const double K = a.K[i], T = a.T[i];
       double F, P;
       row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
@@ -409,6 +457,24 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS>::kMinBlocks) k_iv_binned(
       }
     }
     __syncthreads();
+    // the partial warps' rows to their carry slots, now that phase 3 has read the slots they
+    // take; the next tile's first barrier orders these copies before its phase 1
+    const int nmv = s_nmv;
+    for (int m = tid; m < nmv; m += kBlock) {
+      const int src = s_mv_src[m], dst = s_mv_dst[m];
+      s_x[dst] = s_x[src];
+      s_bmax[dst] = s_bmax[src];
+      s_e[dst] = s_e[src];
+      s_bn[dst] = s_bn[src];
+      s_bsn[dst] = s_bsn[src];
+      s_bb[dst] = s_bb[src];
+      if (kBS) {
+        s_er[dst] = s_er[src];
+        s_ec[dst] = s_ec[src];
+      }
+      s_gidx[dst] = base + (src - kCarry);
+    }
+    if (tid < kBins) s_ccnt[tid] = s_cnt[tid] - s_full[tid];
   }
 }
 
@@ -434,8 +500,8 @@ int launch_binned(const Args& a, void* stream) {
   // occupancy of this instantiation, looked up once per device
   static thread_local int configured_device = -1;
   static thread_local int blocks_per_sm = 0, num_sms = 0;
-  constexpr size_t smem = TileCfg<kBS>::kSmem;
-  constexpr int kTile = TileCfg<kBS>::kTile;
+  constexpr size_t smem = TileCfg<kBS, kMixed>::kSmem;
+  constexpr int kTile = TileCfg<kBS, kMixed>::kTile;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
   if (configured_device != dev) {
