@@ -487,8 +487,12 @@ def run_ours(args, rank, world):
     # ---- end to end through the public API with pinned host buffers
     hF, hK, hT, hP = (t.cpu().pin_memory() for t in (F, K, T, P))
     hflag = flag.cpu().pin_memory()
-    for _ in range(2):
-        pv.iv_forward_backward(hF, hK, hT, hP, hflag, tau=TAU, gate=GATE)
+    # warm-up in the timed loop's pattern (the previous result held during the next call), so
+    # that the pinned-memory cache holds both output sets before timing: the first call that
+    # needs the second set pins ~0.7 GB of host memory (~46 ms once)
+    res = None
+    for _ in range(3):
+        res = pv.iv_forward_backward(hF, hK, hT, hP, hflag, tau=TAU, gate=GATE)
     torch.cuda.synchronize()
     e2e_steps = max(min(args.steps, 5), 1)
     t0 = time.perf_counter()

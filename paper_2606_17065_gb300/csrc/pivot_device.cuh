@@ -494,7 +494,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R dGl = R(3) * bl * (R(kInvSqrt2Pi) * eal) * al / (sl * ul * bsl);
       const R r = shape_monotone<R>(ul, R(0), Gl, R(1), dGl);
       const R G = M::fmin_(rational_cubic<R>(u, R(0), ul, R(0), Gl, R(1), dGl, r), R(0.5));
-      return ax * R(kInvSqrt3) / neg_ncdfinv<R>(G, kFastInv && beta >= R(kDeepBeta));
+      return ax * R(kInvSqrt3) / neg_ncdfinv<R>(G, kFastInv && double(beta) >= kDeepBeta);
     }
     case kMidLow: {
       // rational cubic in b on [b_l, b_c], zero curvature of s(b) at the inflection b_c
