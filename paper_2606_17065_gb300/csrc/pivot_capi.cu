@@ -157,9 +157,10 @@ template <bool kBS, bool kMixed>
 struct TileCfg {
   static constexpr int kBins = kMixed ? 12 : 8;
   static constexpr int kCarry = kCarryPerBin * kBins;
-  static constexpr int kTile = kBS ? (kMixed ? 1024 : 1280) : (kMixed ? 1536 : 1792);
+  static constexpr int kThreads = 256;
   static constexpr int kMinBlocks = 2;
-  static constexpr int kRowsPerThread = kTile / kBlock;
+  static constexpr int kTile = kBS ? (kMixed ? 1024 : 1280) : (kMixed ? 1536 : 1792);
+  static constexpr int kRowsPerThread = kTile / kThreads;
   static constexpr int kSlots = kCarry + kTile;
   static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kSlots * sizeof(double) + size_t(kCarry) * sizeof(int64_t) +
                                   size_t(kSlots) * sizeof(uint16_t) + 2 * size_t(kCarry) * sizeof(uint16_t);
@@ -186,9 +187,11 @@ __device__ __forceinline__ void row_fp(const Args& a, int64_t i, int r, const do
 }
 
 template <bool kBackward, bool kMixed, bool kBS>
-__global__ void __launch_bounds__(kBlock, TileCfg<kBS, kMixed>::kMinBlocks) k_iv_binned(Args a) {
+__global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, kMixed>::kMinBlocks)
+    k_iv_binned(Args a) {
   using Cfg = TileCfg<kBS, kMixed>;
   constexpr int kRowsPerThread = Cfg::kRowsPerThread;
+  constexpr int kThreads = Cfg::kThreads;
   constexpr int kBins = Cfg::kBins;
   constexpr int kCarry = Cfg::kCarry;
   constexpr int kSlots = Cfg::kSlots;
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS, kMixed>::kMinBlocks) k_iv
   // rows per tile for this launch: the launcher shrinks tiles on small batches so that
   // every SM gets work; the shared arrays keep their kTile strides
   const int tile = a.tile;
-  const int jmax = tile / kBlock;
+  const int jmax = tile / kThreads;
   if (tid < kBins) s_ccnt[tid] = 0;
   for (int64_t base = int64_t(blockIdx.x) * tile; base < a.n; base += int64_t(gridDim.x) * tile) {
     const bool last = base + int64_t(gridDim.x) * tile >= a.n;  // the block's last tile takes every row
@@ -231,8 +234,8 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS, kMixed>::kMinBlocks) k_iv
     // ---- phase 1
 #pragma unroll
     for (int j = 0; j < kRowsPerThread; ++j) {
-      const int r = kCarry + j * kBlock + tid;  // slot
-      const int64_t i = base + (j * kBlock + tid);
+      const int r = kCarry + j * kThreads + tid;  // slot
+      const int64_t i = base + (j * kThreads + tid);
       bool solve = false;
       if (j < jmax && i < a.n) {
         const double K = a.K[i], T = a.T[i];
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS, kMixed>::kMinBlocks) k_iv
     int reg[kRowsPerThread], pos[kRowsPerThread], row[kRowsPerThread];
 #pragma unroll
     for (int j = 0; j < kRowsPerThread; ++j) {
-      const int qi = j * kBlock + tid;
+      const int qi = j * kThreads + tid;
       int rg = -1;
       row[j] = 0;
       if (qi < nsolve) {
@@ -362,14 +365,14 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS, kMixed>::kMinBlocks) k_iv
       }
     }
     // carried rows hold the first positions of their bins; those not consumed stay in place
-    for (int c = tid; c < kCarry; c += kBlock) {
+    for (int c = tid; c < kCarry; c += kThreads) {
       const int b = c / kCarryPerBin, p = c - b * kCarryPerBin;
       if (p < s_ccnt[b] && p < s_full[b]) s_order[s_off[b] + p] = uint16_t(c);
     }
     __syncthreads();
     // ---- phase 3
     const int total = s_off[kBins];
-    for (int qi = tid; qi < total; qi += kBlock) {
+    for (int qi = tid; qi < total; qi += kThreads) {
       const int r = s_order[qi];  // slot
       int bin = 0;
 #pragma unroll
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(kBlock, TileCfg<kBS, kMixed>::kMinBlocks) k_iv
     // the partial warps' rows to their carry slots, now that phase 3 has read the slots they
     // take; the next tile's first barrier orders these copies before its phase 1
     const int nmv = s_nmv;
-    for (int m = tid; m < nmv; m += kBlock) {
+    for (int m = tid; m < nmv; m += kThreads) {
       const int src = s_mv_src[m], dst = s_mv_dst[m];
       s_x[dst] = s_x[src];
       s_bmax[dst] = s_bmax[src];
@@ -502,13 +505,14 @@ int launch_binned(const Args& a, void* stream) {
   static thread_local int blocks_per_sm = 0, num_sms = 0;
   constexpr size_t smem = TileCfg<kBS, kMixed>::kSmem;
   constexpr int kTile = TileCfg<kBS, kMixed>::kTile;
+  constexpr int kThreads = TileCfg<kBS, kMixed>::kThreads;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
   if (configured_device != dev) {
     const void* f = reinterpret_cast<const void*>(k_iv_binned<kBackward, kMixed, kBS>);
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kThreads, smem);
     cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     blocks_per_sm = b < 1 ? 1 : b;
     configured_device = dev;
@@ -516,13 +520,13 @@ int launch_binned(const Args& a, void* stream) {
   const int64_t cap = int64_t(blocks_per_sm) * num_sms;
   // the largest tile (a multiple of the block) that still gives every resident block a tile
   int64_t tile = (a.n + cap - 1) / cap;
-  tile = ((tile + kBlock - 1) / kBlock) * kBlock;
+  tile = ((tile + kThreads - 1) / kThreads) * kThreads;
   if (tile > kTile) tile = kTile;
   Args b = a;
   b.tile = int(tile);
   const int64_t tiles = (a.n + tile - 1) / tile;
   const unsigned grid = unsigned(tiles < cap ? tiles : cap);
-  k_iv_binned<kBackward, kMixed, kBS><<<grid, kBlock, smem, static_cast<cudaStream_t>(stream)>>>(b);
+  k_iv_binned<kBackward, kMixed, kBS><<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(b);
   return launch_status();
 }
 
