@@ -75,11 +75,13 @@ struct InferSmem {
   float s0[kITile];
   uint16_t list[kITile], order[kITile], pos[kITile], fb[kITile];
   uint8_t bin[kITile];
-  int nsolve, nfb, cnt[4], off[5];
+  int nsolve, nfb, cnt[6], off[7];
 };
-// bins 0-2: the MLP-seeded objectives; bin 3: deep lower-tail rows (beta below
-// the float range, |x| >= 0.1), seeded in float from ln beta as in the mixed form
-constexpr int kIBins = 4;
+// bins 0-2: the MLP-seeded objectives (lower, b - beta, upper); bin 3: deep lower-tail rows
+// (beta below the float range, |x| >= 0.1), seeded in float from ln beta as in the mixed form;
+// bins 4, 5: the rows of bins 0, 1 near the money (|x| <= kTaylorX), the only ones whose b may
+// take the Taylor series of rho, so that a warp runs one form of rho
+constexpr int kIBins = 6;
 
 template <bool kBackward>
 __device__ __forceinline__ void finish_row(const Args& a, int64_t i, double F, double K, double T, int fl, double s,
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
     if (tid == 0) {
       S.nsolve = 0;
       S.nfb = 0;
-      S.cnt[0] = S.cnt[1] = S.cnt[2] = S.cnt[3] = 0;
+      for (int k = 0; k < kIBins; ++k) S.cnt[k] = 0;
     }
     __syncthreads();
     // ---- phase 1
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
           const float e = erfcxf(sqrtf(f0));
           const bool low = bf <= 0.5f * float(bmax) * (1.0f - e);
           bin = low ? 0 : (beta <= betac ? 1 : 2);
+          if (bin < 2 && x >= -pivot::kTaylorX) bin += 4;
           if (!(s0 > 0.0f && s0 < INFINITY)) bin = -1;
           S.s0[r] = s0;
           S.bb[r] = (bin == 2) ? betac : beta;
@@ -204,7 +207,10 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
     const int total = S.off[kIBins];
     for (int qi = tid; qi < total; qi += kIBlock) {
       const int r = S.order[qi];
-      if (qi >= S.off[3]) {
+      int b = 0;
+#pragma unroll
+      for (int k = 1; k < kIBins; ++k) b += (qi >= S.off[k]) ? 1 : 0;
+      if (b == 3) {
         // deep lower tail
         pivot::Last last;
         const double x = S.x[r], bmax = S.bmax[r];
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
         }
         continue;
       }
-      const int bn = (qi >= S.off[2]) ? 2 : (qi >= S.off[1]) ? 1 : 0;
+      const int bn = b >= 4 ? b - 4 : b;
       const int rg = bn == 0 ? pivot::kLower : bn == 1 ? pivot::kMidHigh : pivot::kUpper;
       const double x = S.x[r], bb = S.bb[r], bmax = S.bmax[r];
       const float xf = float(x), bbf = float(bb);
