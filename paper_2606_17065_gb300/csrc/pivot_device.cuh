@@ -314,9 +314,15 @@ __device__ __forceinline__ bool bad_inputs(double F, double K, double T, int fla
   return !pos_finite(F) || !pos_finite(K) || !pos_finite(T) || (flag != 1 && flag != -1);
 }
 
-// P - F + K (call) or P - K + F (put) with two error-free TwoSums, one rounding
+// P - F + K (call) or P - K + F (put), in the money: P - a + b with a > b > 0, rounded once.
+// By Sterbenz's lemma a - b is exact when a <= 2b, and P - a is exact when a/2 <= P <= 2a, so
+// one of P - (a - b) and (P - a) + b takes a single rounding on every price in or near the
+// no-arbitrage interval [a - b, a]; two error-free TwoSums cover the rest (a > 2b and P below
+// a/2, a price far under the intrinsic value).  Positive doubles compare as their bit patterns.
 __device__ __forceinline__ double time_value_itm(double P, double a, double b) {
-  // P - a + b
+  const double two_b = b + b, half_a = 0.5 * a;
+  if (__double_as_longlong(a) <= __double_as_longlong(two_b)) return P - (a - b);
+  if (__double_as_longlong(P) >= __double_as_longlong(half_a)) return (P - a) + b;
   double s1 = P - a, bb = s1 - P;
   double e1 = (P - (s1 - bb)) + (-a - bb);
   double s2 = s1 + b;
