@@ -285,7 +285,10 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         const double rsq = rsqrt(F * K);
         const double beta = s_bb[r] * rsq, betac = s_e[r] * rsq;
         bool fp64_row = true;
-        if (kMixed && !(beta > kMixedFloor) && betac > kMixedFloor && x > -kMixedMaxAbsX && x <= -kDeepMinAbsX &&
+        // range tests on bit patterns (beta, beta_c and -x are non-negative): integer instructions
+        const bool beta_f = pivot::gt_pos(beta, kMixedFloor), betac_f = pivot::gt_pos(betac, kMixedFloor);
+        const bool x_f = pivot::gt_pos(kMixedMaxAbsX, -x);
+        if (kMixed && !beta_f && betac_f && x_f && !pivot::gt_pos(kDeepMinAbsX, -x) &&
             pivot::pos_normal(beta)) {
           // deep lower tail: beta below the float range but ln beta is not (at |x| >= 0.1 such a
           // beta lies below b_l, in the lower region)
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
           s_x[r] = x;
           s_bmax[r] = bmax;
           s_bb[r] = beta;
-        } else if (kMixed && beta > kMixedFloor && betac > kMixedFloor && x > -kMixedMaxAbsX) {
+        } else if (kMixed && beta_f && betac_f && x_f) {
           // float node and region; the float copies are exact in double storage
           pivot::Node<float> nf;
           rg = pivot::classify<float>(float(x), float(bmax), float(beta), float(betac), nf);
@@ -322,13 +325,13 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         }
         // lower and middle rows near the money to their own bins (FP64 form: 0, 1, 2 -> 7, 4, 5;
         // mixed float: 0, 1, 2 -> 11, 9, 10)
-        if (x >= -pivot::kTaylorX) {
+        if (pivot::le_pos(-x, pivot::kTaylorX)) {
           if (!kMixed && (rg == pivot::kMidLow || rg == pivot::kMidHigh)) rg += 3;
           else if (!kMixed && rg == pivot::kLower) rg = 7;
           if (kMixed && !fp64_row && (rg == pivot::kMidLow || rg == pivot::kMidHigh)) rg += 8;
           else if (kMixed && !fp64_row && rg == pivot::kLower) rg = 11;
         }
-        if (!kMixed && (rg == pivot::kLower || rg == 7) && beta < pivot::kDeepBeta) rg = 6;
+        if (!kMixed && (rg == pivot::kLower || rg == 7) && pivot::gt_pos(pivot::kDeepBeta, beta)) rg = 6;
         row[j] = r;
       }
       reg[j] = rg;
