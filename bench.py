@@ -44,9 +44,9 @@ BYTES_PER_ROW = 33 + 41
 # over one launch of 4,194,304 stress rows, divided by the rows), see
 # profiles/k_iv_binned_fwdbwd_stress.md.  Counts scale with the rows: every
 # launch of the same distribution does the same work per row on average.
-FLOPS_PER_ROW = 400.4
+FLOPS_PER_ROW = 400.8
 # dram__bytes_read.sum + dram__bytes_write.sum per row from the same capture.
-TRAFFIC_PER_ROW = 102.94
+TRAFFIC_PER_ROW = 102.91
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA lanes/clk x 2 FLOP
 # (= 1.25 TFLOP/s nominal at 2.07 GHz), scaled by the SM clock seen under load.
 SMS = 152
