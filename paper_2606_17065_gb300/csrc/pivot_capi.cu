@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kBlock) k_bs_iv_backward(Args a) {
 // Forward (and fused forward+backward) with per-tile compaction and region
 // binning.  A block owns a tile of consecutive rows (kTile, or fewer on a batch
 // too small to give every resident block a full tile).
-//  phase 1: every thread classifies tile/kBlock rows (coalesced loads) with
+//  phase 1: every thread classifies tile/kThreads rows (coalesced loads) with
 //           the cheap stage-1 tests; rows that need no solve (invalid, or at
 //           a bound of the price interval) are finished at once, the others
 //           are appended to a tile-local list (one warp-aggregated atomic).
