@@ -77,7 +77,7 @@ def _host_result(inputs, outs):
 # chunks of this size on three CUDA streams, so that the host-to-device copy of
 # one chunk, the kernels of the next and the device-to-host copy of a third
 # overlap.
-HOST_CHUNK = 1 << 21
+HOST_CHUNK = 1 << 20
 HOST_STREAMS = 3
 _streams = {}
 
@@ -102,6 +102,17 @@ def _host_tensor(t, dtype):
     return t.contiguous()
 
 
+def _pinned_outputs(n, dtypes):
+    """Host outputs of n rows each as views of one pinned allocation (one request to the
+    pinned-memory cache rather than one per output), each view 64-byte aligned."""
+    offs, total = [], 0
+    for d in dtypes:
+        offs.append(total)
+        total += -(-n * torch.empty((), dtype=d).element_size() // 64) * 64
+    buf = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+    return [buf[o:o + n * torch.empty((), dtype=d).element_size()].view(d) for o, d in zip(offs, dtypes)]
+
+
 def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args):
     """Run one row-wise entry point.  `build_args(m, ins, outs)` returns its
     arguments for m rows of device tensors, stream excluded.  Device inputs
@@ -120,7 +131,7 @@ def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args):
     dev = _device_of()
     hins = [_host_tensor(t, d) for t, d in zip(inputs, in_dtypes)]
     _check_lengths(n, *hins)
-    houts = [torch.empty(n, dtype=d, pin_memory=True) for d in out_dtypes]
+    houts = _pinned_outputs(n, out_dtypes)
     streams = _copy_streams(dev)
     bufs = [([None if h is None else torch.empty(HOST_CHUNK, dtype=h.dtype, device=dev) for h in hins],
              [torch.empty(HOST_CHUNK, dtype=d, device=dev) for d in out_dtypes]) for _ in streams]
