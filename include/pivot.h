@@ -288,7 +288,9 @@ int pivot_mlp_adam(pivot_mlp_trainer* trainer, double lr, double beta1, double b
  * 2^26 rows per call (FP32 sums over more rows lose their last digits):
  * larger n returns PIVOT_E_TOO_MANY and launches nothing.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture.
+ * that device current); make that first call before any stream capture.  The
+ * address is kept for the life of the process: do not call this entry point
+ * after a cudaDeviceReset of a device it has already been used on.
  */
 int pivot_mlp_grad_static(const pivot_mlp* net, int64_t n, const double* F, const double* K,
                           const double* T, const double* P, const int8_t* flag, const double* sigma,

@@ -2,6 +2,7 @@
 // cores (mma.sync, FP32 accumulation), FP64 Householder(3) steps on the LBR
 // objectives (appendix stage 5), the gated adjoint, and the training kernels
 // of the MLP (forward, backward and Adam, all in this file).
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -368,14 +369,20 @@ struct TrainSmem {
   M::TrainTiles tiles[kLWarps];
 };
 
-__global__ void __launch_bounds__(kLBlock, 1) k_mlp_grad(pivot_mlp_trainer* tr, int64_t n, const double* __restrict__ F,
-                                                         const double* __restrict__ K, const double* __restrict__ T,
-                                                         const double* __restrict__ P, const int8_t* __restrict__ flag,
-                                                         const double* __restrict__ sigma) {
+// The MLP gradient pass over n rows (forward + backward on tensor cores): the
+// gradient of the sum of squared errors is added to grad[], the sum to
+// *loss_sum and the row count to *rows.  Shared by pivot_mlp_grad (the
+// trainer's own accumulators) and pivot_mlp_grad_static (the library's
+// static scratch).
+__device__ __forceinline__ void mlp_grad_rows(const pivot_mlp* net, int64_t n, const double* __restrict__ F,
+                                              const double* __restrict__ K, const double* __restrict__ T,
+                                              const double* __restrict__ P, const int8_t* __restrict__ flag,
+                                              const double* __restrict__ sigma, float* grad, double* loss_sum,
+                                              double* rows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  M::stage_weights(&tr->net, S.W, &S.WT);
+  M::stage_weights(net, S.W, &S.WT);
   __syncthreads();
   float sq = 0.0f;
   int nvalid = 0;
@@ -397,7 +404,7 @@ __global__ void __launch_bounds__(kLBlock, 1) k_mlp_grad(pivot_mlp_trainer* tr, 
         }
       }
     }
-    sq += M::train_warp(f0, f1, y, valid, S.W, S.WT, S.tiles[warp], tr->grad);
+    sq += M::train_warp(f0, f1, y, valid, S.W, S.WT, S.tiles[warp], grad);
     nvalid += valid ? 1 : 0;
   }
 #pragma unroll
@@ -406,9 +413,16 @@ __global__ void __launch_bounds__(kLBlock, 1) k_mlp_grad(pivot_mlp_trainer* tr, 
     nvalid += __shfl_xor_sync(0xffffffffu, nvalid, off);
   }
   if (lane == 0) {
-    atomicAdd(&tr->loss_sum, double(sq));
-    atomicAdd(&tr->rows, double(nvalid));
+    atomicAdd(loss_sum, double(sq));
+    atomicAdd(rows, double(nvalid));
   }
+}
+
+__global__ void __launch_bounds__(kLBlock, 1) k_mlp_grad(pivot_mlp_trainer* tr, int64_t n, const double* __restrict__ F,
+                                                         const double* __restrict__ K, const double* __restrict__ T,
+                                                         const double* __restrict__ P, const int8_t* __restrict__ flag,
+                                                         const double* __restrict__ sigma) {
+  mlp_grad_rows(&tr->net, n, F, K, T, P, flag, sigma, tr->grad, &tr->loss_sum, &tr->rows);
 }
 
 __global__ void k_mlp_adam(pivot_mlp_trainer* tr, double lr, double beta1, double beta2, double eps) {
@@ -579,44 +593,8 @@ __global__ void __launch_bounds__(kLBlock, 1)
     k_mlp_grad_static(const pivot_mlp* net, int64_t n, const double* __restrict__ F, const double* __restrict__ K,
                       const double* __restrict__ T, const double* __restrict__ P, const int8_t* __restrict__ flag,
                       const double* __restrict__ sigma, float* scratch) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  M::stage_weights(net, S.W, &S.WT);
-  __syncthreads();
-  float sq = 0.0f;
-  int nvalid = 0;
-  for (int64_t c0 = (int64_t(blockIdx.x) * kLWarps + warp) * 32; c0 < n; c0 += int64_t(gridDim.x) * kLWarps * 32) {
-    const int64_t i = c0 + lane;
-    bool valid = false;
-    float f0 = 0.0f, f1 = 0.5f, y = 0.0f;
-    if (i < n) {
-      const double sg = sigma[i];
-      const pivot::Quote q = pivot::classify_quote(F[i], K[i], T[i], P[i], flag[i]);
-      if (q.status == 0 && sg > 0.0 && sg < INFINITY) {
-        const LearnedRow row = learned_row(F[i], K[i], T[i], P[i], flag[i]);
-        const double target = log(sg * sqrt(T[i]) / row.f.sa);
-        if (row.f.sa > 0.0 && fabs(target) < 1e30) {
-          valid = true;
-          f0 = row.f.f0;
-          f1 = row.f.f1;
-          y = float(target);
-        }
-      }
-    }
-    sq += M::train_warp(f0, f1, y, valid, S.W, S.WT, S.tiles[warp], scratch);
-    nvalid += valid ? 1 : 0;
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    sq += __shfl_xor_sync(0xffffffffu, sq, off);
-    nvalid += __shfl_xor_sync(0xffffffffu, nvalid, off);
-  }
-  if (lane == 0) {
-    double* loss = reinterpret_cast<double*>(scratch + kStaticLossOffset);
-    atomicAdd(loss, double(sq));
-    atomicAdd(loss + 1, double(nvalid));
-  }
+  double* loss = reinterpret_cast<double*>(scratch + kStaticLossOffset);
+  mlp_grad_rows(net, n, F, K, T, P, flag, sigma, scratch, loss, loss + 1);
 }
 
 __global__ void k_static_scratch_copy_out(const float* scratch, float* grad_out, double* loss_out) {
@@ -626,21 +604,27 @@ __global__ void k_static_scratch_copy_out(const float* scratch, float* grad_out,
     loss_out[threadIdx.x] = reinterpret_cast<const double*>(scratch + kStaticLossOffset)[threadIdx.x];
 }
 
-// device address of the static scratch, looked up once per device with that device current
+// device address of the static scratch, looked up once per device with that device current.
+// Host threads may make their first call on a device at the same time: each slot is an atomic,
+// and a lookup that loses the race stores the same address.  The cache assumes the device's
+// context lives as long as the process (after cudaDeviceReset the module, and so the array, may
+// be loaded at another address).
 int static_scratch(float** out) {
   constexpr int kMaxDevices = 64;
-  static float* addr[kMaxDevices] = {};
+  static std::atomic<float*> addr[kMaxDevices];
   int dev = 0;
   const cudaError_t e0 = cudaGetDevice(&dev);
   if (e0 != cudaSuccess) return -int(e0);
   if (dev < 0 || dev >= kMaxDevices) return PIVOT_E_NOT_DEVICE;
-  if (addr[dev] == nullptr) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_mlp_grad_scratch);
+  float* p = addr[dev].load(std::memory_order_acquire);
+  if (p == nullptr) {
+    void* q = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&q, g_mlp_grad_scratch);
     if (e != cudaSuccess) return -int(e);
-    addr[dev] = static_cast<float*>(p);
+    p = static_cast<float*>(q);
+    addr[dev].store(p, std::memory_order_release);
   }
-  *out = addr[dev];
+  *out = p;
   return PIVOT_OK;
 }
 
