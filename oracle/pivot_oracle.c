@@ -362,8 +362,15 @@ typedef struct {
   double lnb;      /* ln beta   (beta   = tv/sqrt(FK)) */
   double lnbc;     /* ln beta_c (beta_c = (U - P)/sqrt(FK)) */
   double beta, betac; /* the same, unlogged (0 where they underflow) */
+  double beta_hi;  /* beta 2^BETA_SCALE_EXP where beta is subnormal (tv 2^BETA_SCALE_EXP / sqrt(FK)), else 0 */
   int upper;       /* solve on the complement */
 } solve_t;
+
+/* A subnormal beta is compared with b through this exact power-of-two scaling:
+ * ln b - ln beta as a difference of logarithms would carry an absolute error
+ * ~ eps |ln beta| ~ 700 eps, which near the money (where d ln b / d ln s ~ 1)
+ * is a relative error of ~700 eps in the root. */
+#define BETA_SCALE_EXP 600
 
 /* objective g(s), increasing in s, and its s-derivative; returns 0 when the
  * cheap bound alone decided the sign (deriv is then unset) */
@@ -382,6 +389,8 @@ static int objective(const solve_t* q, double s, double* g, double* dg) {
     /* ln(b/beta): as the log of one ratio when everything is representable
      * (absolute error ~ eps), else as a sum of logarithms */
     if (lbs > -700.0 && q->beta > 0.0) *g = log(exp(lbs) * r / q->beta);
+    else if (lbs > -700.0 && q->beta_hi > 0.0 && r < 1e100)
+      *g = log(ldexp(r, BETA_SCALE_EXP) * exp(lbs) / q->beta_hi); /* r 2^600 is exact */
     else *g = lbs + log(r) - q->lnb;
     *dg = 1.0 / r;
     return 1;
@@ -437,6 +446,7 @@ static void iv_row(double F, double K, double T, double P, int8_t flag, double* 
   q.lnbc = betac >= DBL_MIN ? log(betac) : log(cv) - log(rfk);
   q.beta = beta >= DBL_MIN ? beta : 0.0;
   q.betac = betac >= DBL_MIN ? betac : 0.0;
+  q.beta_hi = beta >= DBL_MIN ? 0.0 : ldexp(tv, BETA_SCALE_EXP) / rfk;
   q.upper = q.lnb > q.lnbc; /* beta > b_max/2 */
   double s = solve_s(&q);
   *sig = s / sqrt(T);

@@ -43,22 +43,29 @@ def vega(F, K, T, sigma):
     return F * mp.npdf(d1) * mp.sqrt(T)
 
 
-def implied_vol(F, K, T, P, theta, iters: int = 200):
+def implied_vol(F, K, T, P, theta, iters: int = 200, lo_sigma="1e-12"):
     """Root of price(sigma) = P by bisection in ln(sigma) (the price is increasing in sigma).
 
     Works on the inputs exactly as given (decimal values of the doubles), so it
-    is the exact real root for those doubles, to ~2^-iters relative.  Returns
-    None outside the open no-arbitrage interval.
+    is the exact real root for those doubles, to about (bracket width in ln
+    sigma) * 2^-iters relative.  The bracket is [lo_sigma, 1e4]; roots of deep
+    lower-tail prices need a floor far below the default.  Returns None outside
+    the open no-arbitrage interval.
     """
     F, K, T, P = map(mp.mpf, (F, K, T, P))
     intrinsic = max(F - K, 0) if theta > 0 else max(K - F, 0)
     upper = F if theta > 0 else K
     if not (intrinsic < P < upper):
         return None
-    lo, hi = mp.log(mp.mpf("1e-12")), mp.log(mp.mpf("1e4"))
+    lo, hi = mp.log(mp.mpf(lo_sigma)), mp.log(mp.mpf("1e4"))
+    ax = abs(mp.log(F / K))
     for _ in range(iters):
         mid = (lo + hi) / 2
-        if price(F, K, T, mp.e ** mid, theta) < P:
+        # |ln(F/K)| / s > 1e4: the time value is below exp(-5e7), far under any positive
+        # double difference P - intrinsic (and mpmath's erfc would overflow there)
+        if ax > 0 and ax > 1e4 * mp.e ** mid * mp.sqrt(T):
+            lo = mid
+        elif price(F, K, T, mp.e ** mid, theta) < P:
             lo = mid
         else:
             hi = mid
