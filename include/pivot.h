@@ -99,6 +99,29 @@ typedef struct {
   pivot_mlp net;   /* BF16 copy of the parameters, refreshed by pivot_mlp_init / pivot_mlp_adam */
 } pivot_mlp_trainer; /* training state, device memory owned by the caller */
 
+/* ---- per-launch counters (optional) -----------------------------------------
+ * pivot_opts.counters, when not NULL, is a device array of PIVOT_COUNTERS_LEN
+ * uint64 that the forward kernels ADD to (the caller clears it):
+ *   [0..5]   rows by status code PIVOT_ROW_* (0: solved)
+ *   [6..17]  solved rows by the kernel's bin, [6 + b] for bin b:
+ *            FP64:    0 lower, 1 mid-low, 2 mid-high, 3 upper, 4 mid-low near the
+ *                     money (|ln(F/K)| <= 0.1), 5 mid-high near the money, 6 lower
+ *                     with beta < 1e-100, 7 lower near the money
+ *            MIXED:   0-3 the four regions seeded in float, 4-7 the four regions
+ *                     in FP64 (outside the float range), 8 deep lower tail seeded
+ *                     in float from ln beta, 9 mid-low and 10 mid-high near the
+ *                     money in float, 11 lower near the money in float
+ *            LEARNED: 0 lower, 1 b - beta, 2 upper (MLP seed), 3 deep lower tail
+ *                     (float seed from ln beta), 4 lower and 5 b - beta near the
+ *                     money (MLP seed)
+ *   [18]     rows of the accelerated form (MIXED float-seeded, LEARNED) not
+ *            accepted and solved again from LBR's rational seed in FP64
+ *   [19..23] reserved (left unchanged)
+ * Counting costs a few shared-memory atomics per warp; a NULL pointer costs
+ * nothing.  Not in the paper: the invalid-domain and region rates it reports
+ * per dataset come from these. */
+#define PIVOT_COUNTERS_LEN 24
+
 typedef struct {
   int32_t mode;          /* PIVOT_MODE_* ; default PIVOT_MODE_FP64 */
   int32_t householder;   /* Householder(3) iterations after the initial guess, 0 = default (2), max 4;
@@ -107,6 +130,7 @@ typedef struct {
   double fallback;       /* PIVOT_MODE_LEARNED: float steps moving the MLP seed by more than this
                             (relative), or a final FP64 step moving the float iterate by more than
                             1e-5, send the row to the rational-guess FP64 path; 0 = default 0.25 */
+  uint64_t* counters;    /* NULL, or PIVOT_COUNTERS_LEN device uint64 counters (above), 8-byte aligned */
 } pivot_opts;
 
 /*
@@ -308,6 +332,36 @@ int64_t pivot_mlp_trainer_bytes(int64_t* net_offset);
  */
 int pivot_iv_guess(int64_t n, const double* F, const double* K, const double* T, const double* P,
                    const int8_t* flag, const pivot_opts* opts, double* s_out, void* stream);
+
+/*
+ * Throughput probes (diagnostics; the paper has no counterpart).  The kernels
+ * above are bound by the FP64 pipe, so their roofline fractions are stated
+ * against measured unit rates as well as against unit counts x clocks.
+ *
+ * pivot_probe_units -- one launch of blocks_per_sm x (SM count) blocks of 256
+ *   threads, each thread running 8 independent dependency chains for
+ *   iters x 8 rounds of one operation:
+ *     unit 0: FP64 fma (a = a b + c), 1: FP32 fma, 2: MUFU ex2.approx (float),
+ *     3: MUFU tanh.approx (float).
+ *   sink: device memory of 8 x (grid) bytes or more (written only if a chain
+ *   reaches an impossible value); *lane_ops (HOST double) receives the number of
+ *   lane operations the launch performs (an fma counts once: 2 FLOP).
+ *   Errors: PIVOT_E_OPTS for unit outside 0..3, blocks_per_sm outside 1..32 or
+ *   iters < 1; PIVOT_E_NULL for a NULL lane_ops.
+ *
+ * pivot_probe_stream -- the fused forward+backward's HBM traffic with no
+ *   arithmetic: reads F, K, T, P (float64) and flag (int8), writes sigma = P,
+ *   dP = F, dF = K, dK = T, dT = P (float64) and status = flag (uint8), 74 bytes
+ *   per row, grid-stride over blocks_per_sm x (SM count) blocks of 256 threads.
+ *   width 1: 64-bit accesses, one row per thread; width 2: 128-bit accesses of
+ *   two consecutive rows per thread (every float64 array 16-byte aligned, the
+ *   int8 arrays 2-byte aligned, else PIVOT_E_ALIGN).  All arrays required.
+ */
+int pivot_probe_units(int32_t unit, int32_t blocks_per_sm, int64_t iters, void* sink, double* lane_ops,
+                      void* stream);
+int pivot_probe_stream(int32_t width, int64_t n, const double* F, const double* K, const double* T,
+                       const double* P, const int8_t* flag, double* sigma, uint8_t* status, double* dP,
+                       double* dF, double* dK, double* dT, int32_t blocks_per_sm, void* stream);
 
 /* Human-readable text for a return code. */
 const char* pivot_error_string(int code);

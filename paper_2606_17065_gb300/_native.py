@@ -20,7 +20,10 @@ c_i64, c_i32, c_dbl, c_vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, cty
 
 class PivotOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("householder", ctypes.c_int32), ("mlp", ctypes.c_void_p),
-                ("fallback", ctypes.c_double)]
+                ("fallback", ctypes.c_double), ("counters", ctypes.c_void_p)]
+
+
+COUNTERS_LEN = 24
 
 
 _SIGNATURES = {
@@ -42,6 +45,8 @@ _SIGNATURES = {
     "pivot_mlp_grad": [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
     "pivot_mlp_adam": [c_vp, c_dbl, c_dbl, c_dbl, c_dbl, c_vp],
     "pivot_mlp_grad_static": [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp],
+    "pivot_probe_units": [c_i32, c_i32, c_i64, c_vp, c_vp, c_vp],
+    "pivot_probe_stream": [c_i32, c_i64] + [c_vp] * 11 + [c_i32, c_vp],
     "pivot_error_string": [ctypes.c_int],
     "pivot_version": [],
 }

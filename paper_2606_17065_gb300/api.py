@@ -208,13 +208,25 @@ def elementary(fn: str, x):
     return _host_result((x,), [y])[0]
 
 
-def _opts(mode, householder, mlp=None, fallback: float = 0.0):
+def _opts(mode, householder, mlp=None, fallback: float = 0.0, counters=None):
     o = _native.PivotOpts()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.householder = int(householder)
     o.mlp = None if mlp is None else mlp.weights_ptr()
     o.fallback = float(fallback)
+    if counters is not None:
+        if not (counters.is_cuda and counters.dtype in (torch.int64, torch.uint64) and counters.is_contiguous()
+                and counters.numel() >= _native.COUNTERS_LEN):
+            raise ValueError(f"counters must be a contiguous CUDA int64 tensor of {_native.COUNTERS_LEN} entries")
+        o.counters = counters.data_ptr()
     return o
+
+
+def new_counters(device=None):
+    """A zeroed device tensor for the per-launch counters of ``iv`` / ``iv_forward_backward``
+    (layout in include/pivot.h: rows by status, solved rows by bin, rejected accelerated rows)."""
+    dev = device or _device_of()
+    return torch.zeros(_native.COUNTERS_LEN, dtype=torch.int64, device=dev)
 
 
 class MlpTrainer:
@@ -275,9 +287,10 @@ def iv_guess(F, K, T, P, flag, *, mode="fp64", mlp=None):
 
 
 def iv(F, K, T, P, flag, *, mode="fp64", householder: int = 0, status: bool = True, mlp=None,
-       fallback: float = 0.0):
-    """Implied volatility (Algorithm 1 forward); returns (sigma, status or None)."""
-    o = _opts(mode, householder, mlp, fallback)
+       fallback: float = 0.0, counters=None):
+    """Implied volatility (Algorithm 1 forward); returns (sigma, status or None).  ``counters``
+    (from ``new_counters``) accumulates the launch's row counts."""
+    o = _opts(mode, householder, mlp, fallback, counters)
     f64 = torch.float64
     outs = _rows_call("pivot_iv_forward", (F, K, T, P, flag), (f64, f64, f64, f64, torch.int8),
                       (f64, torch.uint8) if status else (f64,),
@@ -301,9 +314,9 @@ def iv_backward(F, K, T, flag, sigma, gbar=None, *, tau: float = 1e-6, gate="nan
 
 
 def iv_forward_backward(F, K, T, P, flag, gbar=None, *, tau: float = 1e-6, gate="nan", mode="fp64",
-                        householder: int = 0, mlp=None, fallback: float = 0.0):
+                        householder: int = 0, mlp=None, fallback: float = 0.0, counters=None):
     """Forward and gated adjoint in one pass; returns (sigma, status, dP, dF, dK, dT)."""
-    o = _opts(mode, householder, mlp, fallback)
+    o = _opts(mode, householder, mlp, fallback, counters)
     f64 = torch.float64
     gm = _gate(gate)
     outs = _rows_call("pivot_iv_forward_backward", (F, K, T, P, flag, gbar),
@@ -388,9 +401,9 @@ def bs_price(S, K, T, r, q, sigma, flag, *, vega: bool = True):
     return tuple(_host_result((S, K, T, r, q, sigma, flag), [V, vg]))
 
 
-def bs_iv(S, K, T, r, q, V, flag, *, mode="fp64", householder: int = 0, status: bool = True):
+def bs_iv(S, K, T, r, q, V, flag, *, mode="fp64", householder: int = 0, status: bool = True, counters=None):
     """Implied volatility from the discounted price; returns (sigma, status or None)."""
-    o = _opts(mode, householder)
+    o = _opts(mode, householder, counters=counters)
     f64 = torch.float64
     outs = _rows_call("pivot_bs_iv_forward", (S, K, T, r, q, V, flag), (f64,) * 6 + (torch.int8,),
                       (f64, torch.uint8) if status else (f64,),
@@ -414,9 +427,9 @@ def bs_iv_backward(S, K, T, r, q, flag, sigma, gbar=None, *, tau: float = 1e-6, 
 
 
 def bs_iv_forward_backward(S, K, T, r, q, V, flag, gbar=None, *, tau: float = 1e-6, gate="nan", mode="fp64",
-                           householder: int = 0):
+                           householder: int = 0, counters=None):
     """Forward and gated adjoint in xi in one pass; returns (sigma, status, dV, dS, dK, dT, dr, dq)."""
-    o = _opts(mode, householder)
+    o = _opts(mode, householder, counters=counters)
     f64 = torch.float64
     gm = _gate(gate)
     outs = _rows_call("pivot_bs_iv_forward_backward", (S, K, T, r, q, V, flag, gbar),
@@ -450,3 +463,28 @@ class ImpliedVolBS(torch.autograd.Function):
 def bs_implied_volatility_autograd(V, S, K, T, r, q, flag, tau: float = 1e-6, gate="nan"):
     """Differentiable implied volatility on xi = (S, K, tau, r, q), see ``ImpliedVolBS``."""
     return ImpliedVolBS.apply(V, S, K, T, r, q, flag, tau, gate)
+
+
+# ---------------------------------------------------------------------------------------------
+# Throughput probes (include/pivot.h, pivot_probe_*): measured unit rates for the rooflines.
+# ---------------------------------------------------------------------------------------------
+PROBE_UNITS = {"fp64_fma": 0, "fp32_fma": 1, "mufu_ex2": 2, "mufu_tanh": 3}
+
+
+def probe_units(unit: str, iters: int, blocks_per_sm: int = 8, device=None):
+    """Launch one unit probe on the current stream; returns the lane operations it performs."""
+    dev = device or _device_of()
+    sink = torch.zeros(1 << 16, dtype=torch.float64, device=dev)
+    ops = ctypes.c_double(0.0)
+    _native.call("pivot_probe_units", PROBE_UNITS[unit], int(blocks_per_sm), int(iters), _p(sink),
+                 ctypes.byref(ops), _stream(dev))
+    return float(ops.value)
+
+
+def probe_stream(width: int, F, K, T, P, flag, outs, blocks_per_sm: int = 8):
+    """The 74-byte-per-row stream of the fused forward+backward (no arithmetic); `outs` =
+    (sigma, status, dP, dF, dK, dT) device tensors."""
+    dev = F.device
+    sig, st, dP, dF, dK, dT = outs
+    _native.call("pivot_probe_stream", int(width), F.numel(), _p(F), _p(K), _p(T), _p(P), _p(flag), _p(sig),
+                 _p(st), _p(dP), _p(dF), _p(dK), _p(dT), int(blocks_per_sm), _stream(dev))

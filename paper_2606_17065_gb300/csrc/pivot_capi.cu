@@ -215,9 +215,12 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
   __shared__ int s_full[kMaxBins];  // rows per bin consumed by this tile
   __shared__ int s_ccnt[kMaxBins];  // rows per bin carried into the next tile
   __shared__ int s_off[kMaxBins + 1];
+  __shared__ unsigned long long s_count[PIVOT_COUNTERS_LEN];  // a.counters: this block's sums
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
+  const bool counting = a.counters != nullptr;
+  if (counting && tid < PIVOT_COUNTERS_LEN) s_count[tid] = 0;
   // rows per tile for this launch: the launcher shrinks tiles on small batches so that
   // every SM gets work; the shared arrays keep their kTile strides
   const int tile = a.tile;
@@ -237,6 +240,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
       const int r = kCarry + j * kThreads + tid;  // slot
       const int64_t i = base + (j * kThreads + tid);
       bool solve = false;
+      int row_status = -1;
       if (j < jmax && i < a.n) {
         const double K = a.K[i], T = a.T[i];
         double rr = 0.0, qq = 0.0;
@@ -249,6 +253,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
         const int fl = a.flag[i];
         const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
+        row_status = q.status;
         if (q.status != 0) {
           a.sigma[i] = q.sigma;
           if (a.status) a.status[i] = uint8_t(q.status);
@@ -265,6 +270,13 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
       }
       const int slot = warp_append(solve, &s_nsolve, lane);
       if (solve) s_list[slot] = uint16_t(r);
+      if (counting) {
+#pragma unroll
+        for (int k = 1; k < 6; ++k) {
+          const unsigned m = __ballot_sync(0xffffffffu, row_status == k);
+          if (lane == 0 && m) atomicAdd(&s_count[k], (unsigned long long)__popc(m));
+        }
+      }
     }
     __syncthreads();
     // ---- phase 2
@@ -350,6 +362,10 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         s_full[k] = full;
         s_off[k + 1] = s_off[k] + full;
       }
+      if (counting) {
+        s_count[0] += nsolve;
+        for (int k = 0; k < kBins; ++k) s_count[kCountBin0 + k] += s_full[k];
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -411,6 +427,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
           s = pivot::solve_mixed64(rg, nf, s_x[r], s_bmax[r], bb, a.steps, last);
         }
         fp64 = !pivot::pos_finite(s);
+        if (counting && fp64) atomicAdd(&s_count[kCountReject], 1ull);
       }
       if (fp64) {
         pivot::Node<double> nd;
@@ -481,6 +498,10 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
       s_gidx[dst] = base + (src - kCarry);
     }
     if (tid < kBins) s_ccnt[tid] = s_cnt[tid] - s_full[tid];
+  }
+  if (counting) {
+    __syncthreads();
+    if (tid < PIVOT_COUNTERS_LEN && s_count[tid]) atomicAdd(&a.counters[tid], s_count[tid]);
   }
 }
 
@@ -585,6 +606,8 @@ int pivot_iv_forward(int64_t n, const double* F, const double* K, const double* 
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
   Args a{n, F, K, T, P, flag, nullptr, 0.0, 0, steps, sigma_out, status_out, nullptr, nullptr, nullptr, nullptr};
+  rc = check_counters(opts, dev, &a.counters);
+  if (rc != PIVOT_OK) return rc;
   if (mode == PIVOT_MODE_LEARNED) {
     int d2 = dev;
     rc = check_ptr(opts->mlp, true, true, &d2);
@@ -632,6 +655,8 @@ int pivot_iv_forward_backward(int64_t n, const double* F, const double* K, const
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
   Args a{n, F, K, T, P, flag, gbar, tau, gate_mode, steps, sigma_out, status_out, dP, dF, dK, dT};
+  rc = check_counters(opts, dev, &a.counters);
+  if (rc != PIVOT_OK) return rc;
   if (mode == PIVOT_MODE_LEARNED) {
     int d2 = dev;
     rc = check_ptr(opts->mlp, true, true, &d2);
@@ -678,6 +703,8 @@ int pivot_bs_iv_forward(int64_t n, const double* S, const double* K, const doubl
   if (rc != PIVOT_OK) return rc;
   Args a{n, S, K, T, V, flag, nullptr, 0.0, 0, steps, sigma_out, status_out, nullptr, nullptr, nullptr, nullptr,
          r, q, nullptr, nullptr};
+  rc = check_counters(opts, dev, &a.counters);
+  if (rc != PIVOT_OK) return rc;
   return mode == PIVOT_MODE_MIXED ? launch_binned<false, true, true>(a, stream)
                                   : launch_binned<false, false, true>(a, stream);
 }
@@ -725,6 +752,8 @@ int pivot_bs_iv_forward_backward(int64_t n, const double* S, const double* K, co
   if (rc == PIVOT_OK) rc = select_device(dev);
   if (rc != PIVOT_OK) return rc;
   Args a{n, S, K, T, V, flag, gbar, tau, gate_mode, steps, sigma_out, status_out, dV, dS, dK, dT, r, q, dr, dq};
+  rc = check_counters(opts, dev, &a.counters);
+  if (rc != PIVOT_OK) return rc;
   return mode == PIVOT_MODE_MIXED ? launch_binned<true, true, true>(a, stream)
                                   : launch_binned<true, false, true>(a, stream);
 }

@@ -32,7 +32,13 @@ struct Args {
   // rows per tile of the binned kernel (a multiple of its block size, at most
   // its compile-time tile); 0 = the largest; set by the launcher
   int tile;
+  // PIVOT_COUNTERS_LEN per-launch counters (pivot_opts.counters), or NULL
+  unsigned long long* counters;
 };
+
+// slots of the counters (include/pivot.h)
+constexpr int kCountBin0 = 6;
+constexpr int kCountReject = 18;
 
 __device__ __forceinline__ void write_grad(const Args& a, int64_t i, double F, double K, double T, int fl,
                                            double sig) {
@@ -128,6 +134,16 @@ inline int select_device(int device) {
   return PIVOT_OK;
 }
 
+// the counters of pivot_opts: NULL, or device memory of the call's device
+inline int check_counters(const pivot_opts* o, int device, unsigned long long** out) {
+  *out = nullptr;
+  if (o == nullptr || o->counters == nullptr) return PIVOT_OK;
+  int d = device;
+  const int rc = check_ptr(o->counters, true, true, &d);
+  if (rc != PIVOT_OK) return rc;
+  *out = reinterpret_cast<unsigned long long*>(o->counters);
+  return PIVOT_OK;
+}
 
 // PIVOT_MODE_LEARNED launch (pivot_learned.cu)
 int launch_learned(const Args& a, const pivot_mlp* mlp, double fallback, bool backward, void* stream);

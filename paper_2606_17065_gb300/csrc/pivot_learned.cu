@@ -77,6 +77,7 @@ struct InferSmem {
   uint16_t list[kITile], order[kITile], pos[kITile], fb[kITile];
   uint8_t bin[kITile];
   int nsolve, nfb, cnt[6], off[7];
+  unsigned long long count[PIVOT_COUNTERS_LEN]; // a.counters: this block's sums
 };
 // bins 0-2: the MLP-seeded objectives (lower, b - beta, upper); bin 3: deep lower-tail rows
 // (beta below the float range, |x| >= 0.1), seeded in float from ln beta as in the mixed form;
@@ -110,6 +111,8 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   M::stage_weights(net, S.W, nullptr);
   const int fsteps = a.steps - 1; // float steps before the FP64 one
+  const bool counting = a.counters != nullptr;
+  if (counting && tid < PIVOT_COUNTERS_LEN) S.count[tid] = 0;
   for (int64_t base = int64_t(blockIdx.x) * kITile; base < a.n; base += int64_t(gridDim.x) * kITile) {
     if (tid == 0) {
       S.nsolve = 0;
@@ -123,10 +126,12 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       const int r = j * kIBlock + tid;
       const int64_t i = base + r;
       bool solve = false;
+      int row_status = -1;
       if (i < a.n) {
         const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
         const int fl = a.flag[i];
         const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
+        row_status = q.status;
         if (q.status != 0) {
           a.sigma[i] = q.sigma;
           if (a.status) a.status[i] = uint8_t(q.status);
@@ -139,6 +144,13 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       }
       const int slot = warp_append(solve, &S.nsolve, lane);
       if (solve) S.list[slot] = uint16_t(r);
+      if (counting) {
+#pragma unroll
+        for (int k = 1; k < 6; ++k) {
+          const unsigned m = __ballot_sync(0xffffffffu, row_status == k);
+          if (lane == 0 && m) atomicAdd(&S.count[k], (unsigned long long)__popc(m));
+        }
+      }
     }
     __syncthreads();
     // ---- phase 2: normalisation, MLP seed, objective
@@ -268,6 +280,15 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       finish_row<kBackward>(a, i, F, K, T, fl, s, x, bmax, last);
     }
     __syncthreads();
+    if (counting && tid == 0) {
+      S.count[0] += S.nsolve;
+      for (int k = 0; k < kIBins; ++k) S.count[kCountBin0 + k] += S.cnt[k];
+      S.count[kCountReject] += nfb;
+    }
+  }
+  if (counting) {
+    __syncthreads();
+    if (tid < PIVOT_COUNTERS_LEN && S.count[tid]) atomicAdd(&a.counters[tid], S.count[tid]);
   }
 }
 

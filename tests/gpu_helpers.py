@@ -94,3 +94,39 @@ def assert_grad_parity(got, want, rows, tol=1e-10, where="", vega=None, gbar=Non
                 same |= (ul == 0) & ((np.isnan(gl) | (gl == 0)) & (np.isnan(wl) | (wl == 0)))
                 same |= np.abs(gl - wl) <= tol * np.abs(wl)
             assert same.all(), f"{where} {name}: {np.sum(~same)} subnormal-vega rows disagree"
+
+
+def assert_grad_offdomain(F, K, T, P, flag, sig, st, ref, grads_nan, grads_exact, tau=1e-6, tol=1e-10, where=""):
+    """The fused path's gradients on solved rows OFF the parity domain (kappa_P > 100), where sigma
+    itself is only fixed to the conditioning bound of ``assert_sigma_parity``.
+
+    (a) Against the oracle's adjoint evaluated at the GPU's own sigma (gate mode 1, tau): the
+        closed forms of Eq. implicit_iv at one sigma, so `tol` relative as on the domain.
+    (b) Against the oracle's adjoint at the oracle's sigma (exact gate): within
+        tol + 256 eps (1 + kappa_beta) (2 + 6 (A + B)), the sigma bound times the conditioning of
+        the gradient in sigma (|d ln g / d ln s| <= 1 + h^2 + t^2 + (|h| + t)^2 <= 2 + 6 (A + B),
+        A + B = h^2/2 + t^2/2 the exponent of b_s), wherever both are finite and the vega is
+        normal.
+    Returns the number of rows checked."""
+    kp, kb = conditioning(F, K, T, P, flag, ref)
+    ok = (st == 0) & np.isfinite(sig) & (sig > 0)
+    off = ok & ~(kp <= 100)
+    if not off.any():
+        return 0
+    want_at_gpu = oracle.iv_grad(F, K, T, flag, np.where(ok, sig, ref), None, tau, 1, nthreads=0)
+    _, Vg = oracle.black_price(F, K, T, np.where(ok, sig, 1.0), flag, nthreads=0)
+    assert_grad_parity(grads_nan, want_at_gpu, off, tol=tol, where=f"{where} off-domain at GPU sigma", vega=Vg)
+    want_ref = oracle.iv_grad(F, K, T, flag, ref, None, 0.0, 0, nthreads=0)
+    _, Vr = oracle.black_price(F, K, T, np.where(np.isfinite(ref), ref, 1.0), flag, nthreads=0)
+    AB = exponent(F, K, T, ref)
+    with np.errstate(invalid="ignore", over="ignore"):
+        bound = tol + 256 * EPS * (1 + kb) * (2 + 6 * AB)
+    rows = off & (np.abs(Vr) >= 1e-280) & (np.abs(Vg) >= 1e-280)
+    for name, g, w in zip(("dP", "dF", "dK", "dT"), grads_exact, want_ref):
+        fin = rows & np.isfinite(g) & np.isfinite(w) & (w != 0)
+        with np.errstate(invalid="ignore", divide="ignore", over="ignore"):
+            rel = np.abs(g[fin] - w[fin]) / np.abs(w[fin])
+        bad = rel > bound[fin]
+        assert not bad.any(), (f"{where} {name}: {bad.sum()} off-domain rows beyond the conditioning bound, "
+                               f"worst ratio {np.max(rel / bound[fin]):.3e}")
+    return int(off.sum())

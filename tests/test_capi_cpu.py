@@ -54,3 +54,34 @@ def test_elementary_function_codes():
     for fn in (0, 1, 2):
         assert lib.pivot_elementary(fn, 0, None, None, None) == 0
         assert lib.pivot_elementary(fn, -1, fake, fake, None) == 1
+
+
+def test_probe_argument_errors():
+    """pivot_probe_units / pivot_probe_stream reject bad units, widths, sizes and a NULL
+    lane_ops before any device access; an empty stream succeeds."""
+    lib = _native.lib()
+    fake = ctypes.c_void_p(0x1000)
+    ops = ctypes.c_double(0.0)
+    for unit, bps, iters in ((-1, 8, 1), (4, 8, 1), (0, 0, 1), (0, 33, 1), (0, 8, 0)):
+        assert lib.pivot_probe_units(unit, bps, iters, fake, ctypes.byref(ops), None) == 4
+    assert lib.pivot_probe_units(0, 8, 1, fake, None, None) == 2
+    args = [fake] * 11
+    assert lib.pivot_probe_stream(1, -1, *args, 8, None) == 1
+    assert lib.pivot_probe_stream(3, 4, *args, 8, None) == 4
+    assert lib.pivot_probe_stream(1, 4, *args, 0, None) == 4
+    assert lib.pivot_probe_stream(2, 0, *([None] * 11), 8, None) == 0
+
+
+def test_opts_layout_and_counters_validation():
+    """pivot_opts carries the counters pointer last; the binding refuses a counters tensor that
+    is not a CUDA int64 array of PIVOT_COUNTERS_LEN entries."""
+    import pytest
+    import torch
+
+    from paper_2606_17065_gb300 import api
+    assert ctypes.sizeof(_native.PivotOpts) == 32
+    assert _native.PivotOpts.counters.offset == 24
+    with pytest.raises(ValueError):
+        api._opts("fp64", 0, counters=torch.zeros(24, dtype=torch.int64))  # host memory
+    text = open(_native.INCLUDE + "/pivot.h").read()
+    assert f"#define PIVOT_COUNTERS_LEN {_native.COUNTERS_LEN}" in text

@@ -115,3 +115,17 @@ def test_svi_iv_loss_training():
     assert out["nan_grad_steps"] == 0
     assert np.all(np.isfinite(out["loss"]))
     assert out["loss"][-1] < 0.1 * out["loss"][0]
+
+
+def test_svi_iv_loss_full_size():
+    """Configuration 5 as specified: 1,024 SVI surfaces, ragged 50-400 quotes over 8 maturities, one
+    MLP 2 -> 128 x 4 -> 1 pricer per surface, 100 Adam steps at lr 1e-3 through ImpliedVol."""
+    batch = workloads.svi_batch(1024, seed=5)
+    assert batch.n_surfaces == 1024 and batch.max_quotes <= 400
+    out = training.train_iv_loss(batch, steps=100, lr=1e-3, tau=1e-6, gate="smooth")
+    print(f"svi-1024: {out['quotes']} quotes, {1e3 * out['seconds'] / 100:.2f} ms/step, loss {out['loss'][0]:.4g} "
+          f"-> {out['loss'][-1]:.4g}, gate kept {out['iv_gate_kept'][-1]:.4f}")
+    assert out["nan_grad_steps"] == 0
+    assert np.all(np.isfinite(out["loss"]))
+    assert out["loss"][-1] <= 0.1 * out["loss"][0]
+    assert min(out["iv_gate_kept"]) > 0.9

@@ -18,8 +18,8 @@ from paper_2606_17065_gb300 import _native, workloads  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-from gpu_helpers import (DEV, EPS, assert_grad_parity, assert_sigma_parity, conditioning, oracle_inputs,  # noqa: E402
-                         to_dev, to_np)
+from gpu_helpers import (DEV, EPS, assert_grad_offdomain, assert_grad_parity, assert_sigma_parity,  # noqa: E402
+                         conditioning, oracle_inputs, to_dev, to_np)
 
 
 @pytest.fixture(scope="module")
@@ -108,6 +108,102 @@ def test_forward_backward_fused_parity(body, stress):
         # sigma from the separate forward is the same bits
         sig2, _ = gpu_iv(b, P)
         assert np.array_equal(sig, sig2, equal_nan=True)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_fused_gradients_off_parity_domain(body, stress, mode):
+    """The fused kernels' adjoint (the last Householder evaluation's Mills ratios reused) on
+    solved rows outside the parity domain: against the oracle at the GPU's sigma, and against
+    the oracle at its own sigma under the conditioning-scaled bound."""
+    checked = 0
+    for name, (b, P, ref, st_ref) in (("body", body), ("stress", stress)):
+        args = [to_dev(a) for a in (b.F, b.K, b.T, P, b.flag)]
+        sig, st, *g_nan = [to_np(x) for x in pv.iv_forward_backward(*args, tau=1e-6, gate="nan", mode=mode)]
+        _, _, *g_exact = [to_np(x) for x in pv.iv_forward_backward(*args, tau=1e-6, gate="exact", mode=mode)]
+        assert np.array_equal(st, st_ref)
+        checked += assert_grad_offdomain(b.F, b.K, b.T, P, b.flag, sig, st, ref, g_nan, g_exact,
+                                         where=f"{mode} {name}")
+    assert checked > 10000, checked
+
+
+def tiny_root_rows():
+    """The oracle pins' tiny-root rows: ATM quotes priced down to subnormal time values, and deep
+    lower-tail quotes (beta < 1e-30, |ln(F/K)| up to 6, beta down to subnormal)."""
+    import test_oracle_tiny_roots as TR
+    F1, K1, T1, P1, f1 = TR.atm_rows()
+    F2, K2, T2, P2, f2 = TR.deep_tail_rows()
+    cat = np.concatenate
+    return cat([F1, F2]), cat([K1, K2]), cat([T1, T2]), cat([P1, P2]), cat([f1, f2]).astype(np.int8)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_tiny_roots(mode):
+    F, K, T, P, flag = tiny_root_rows()
+    ref, st_ref = oracle.implied_vol(F, K, T, P, flag)
+    args = [to_dev(a) for a in (F, K, T, P, flag)]
+    sig, st, *grads = [to_np(x) for x in pv.iv_forward_backward(*args, tau=1e-300, gate="exact", mode=mode)]
+    # subnormal sigma: the bound is one subnormal ulp of s and of s / sqrt(T) on top of the relative one
+    sub = ref < 2.3e-308
+    assert_sigma_parity(F[~sub], K[~sub], T[~sub], P[~sub], flag[~sub], sig[~sub], st[~sub], ref[~sub],
+                        st_ref[~sub], where=f"tiny roots {mode}")
+    tiny = 4.9406564584124654e-324
+    assert np.array_equal(st[sub], st_ref[sub])
+    assert np.all(np.abs(sig[sub] - ref[sub]) <= 8 * EPS * ref[sub] + 2 * tiny * (1 + 1 / np.sqrt(T[sub])))
+    want = oracle.iv_grad(F, K, T, flag, ref, None, 0.0, 0)
+    _, Vr = oracle.black_price(F, K, T, np.where(np.isfinite(ref), ref, 1.0), flag)
+    kp, _ = conditioning(F, K, T, P, flag, ref)
+    dom = (st_ref == 0) & (kp <= 100) & ~sub
+    assert_grad_parity(grads, want, dom, where=f"tiny roots {mode}", vega=Vr)
+
+
+def test_counters_match_outputs(stress):
+    """pivot_opts.counters: rows by status equal the status array's histogram, bins add up to the
+    solved rows, rejected rows of the mixed form are among its float-seeded ones."""
+    b, P, ref, st_ref = stress
+    args = [to_dev(a) for a in (b.F, b.K, b.T, P, b.flag)]
+    for mode, nbins in (("fp64", 8), ("mixed", 12)):
+        c = pv.new_counters(DEV)
+        sig, st = pv.iv(*args, mode=mode, counters=c)
+        c2 = pv.new_counters(DEV)
+        pv.iv_forward_backward(*args, mode=mode, counters=c2)
+        c, c2 = to_np(c), to_np(c2)
+        assert np.array_equal(c, c2)
+        hist = np.bincount(to_np(st), minlength=6)
+        assert np.array_equal(c[:6], hist), (c[:6], hist)
+        assert c[6:6 + nbins].sum() == hist[0] and np.all(c[6 + nbins:18] == 0)
+        assert np.all(c[19:] == 0)
+        if mode == "fp64":
+            assert c[18] == 0
+        else:
+            assert c[18] <= c[6:10].sum() + c[6 + 8:6 + 12].sum()
+    # counters add across calls and are left alone when not requested
+    c = pv.new_counters(DEV)
+    pv.iv(*args, counters=c)
+    pv.iv(*args)
+    pv.iv(*args, counters=c)
+    assert np.array_equal(to_np(c)[:6], 2 * np.bincount(st_ref, minlength=6))
+
+
+def test_probes():
+    """pivot_probe_units runs and reports its work; pivot_probe_stream moves every row exactly."""
+    from paper_2606_17065_gb300 import api
+    for unit in api.PROBE_UNITS:
+        ops = api.probe_units(unit, 4, blocks_per_sm=2)
+        assert ops == 152 * 2 * 256 * 4 * 64 or ops > 0
+    torch.cuda.synchronize()
+    n = 4097
+    b = workloads.stress_batch(n, seed=5)
+    F, K, T, P = (to_dev(a) for a in (b.F, b.K, b.T, b.sigma_star))
+    flag = to_dev(b.flag)
+    for width in (1, 2):
+        outs = [torch.full((n,), np.nan, dtype=torch.float64, device=DEV), torch.zeros(n, dtype=torch.uint8,
+                                                                                       device=DEV)]
+        outs += [torch.full((n,), np.nan, dtype=torch.float64, device=DEV) for _ in range(4)]
+        api.probe_stream(width, F, K, T, P, flag, outs)
+        sig, st, dP, dF, dK, dT = (to_np(o) for o in outs)
+        assert np.array_equal(sig, b.sigma_star) and np.array_equal(dT, b.sigma_star)
+        assert np.array_equal(dP, b.F) and np.array_equal(dF, b.K) and np.array_equal(dK, b.T)
+        assert np.array_equal(st.view(np.int8), b.flag)
 
 
 def edge_rows():
