@@ -83,6 +83,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU oracle sample")
     ap.add_argument("--case", default=None, choices=sorted(FLOPS),
                     help="time one form on --rows rows of its workload only (profiling captures)")
+    ap.add_argument("--probe", action="store_true", help="only the unit throughput probes (profiling captures)")
     return ap.parse_args()
 
 
@@ -884,6 +885,14 @@ def main():
     args = parse()
     if args.case is not None:
         run_case(args)
+        return
+    if args.probe:
+        import torch
+        dev = torch.device("cuda", 0)
+        with ClockSampler(0) as clocks:
+            peaks = unit_peaks(dev, torch.cuda.current_stream(dev), 2070.0)
+        print(json.dumps({"probe": peaks, "clocks": clocks.summary(),
+                          "note": "per_sm_per_clk at 2,070 MHz; see clocks for the sampled SM clock"}), flush=True)
         return
     rank, world = dist_setup(args)
     if args.impl == "reference":

@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         // the adjoint at the solved s, reusing x and 1/sqrt(T) of this row
         const double g = a.gbar ? a.gbar[i] : 1.0;
         const double gate_tau = kBS ? a.tau * s_er[r] : a.tau;  // G_tau on the cash vega e^{-r tau} V
-        const pivot::Grad d = isnan(g) ? pivot::degenerate_grad(true, g, a.mode)
+        const pivot::Grad d = pivot::nan64(g) ? pivot::degenerate_grad(true, g, a.mode)
                                        : pivot::adjoint_reuse(F, K, fl, sig, s, s_x[r], s_bmax[r], inv_sqT,
                                                               rsqrt(F * K), g, gate_tau, a.mode, last);
         if (kBS) {

@@ -165,8 +165,8 @@ struct Math<double> {
   static __device__ __forceinline__ double cbrt_(double v) { return ::cbrt(v); }
   static __device__ __forceinline__ double ncdf_(double v) { return ::normcdf(v); }
   static __device__ __forceinline__ double fma_(double a, double b, double c) { return ::fma(a, b, c); }
-  static __device__ __forceinline__ double fmin_(double a, double b) { return ::fmin(a, b); }
-  static __device__ __forceinline__ double fmax_(double a, double b) { return ::fmax(a, b); }
+  static __device__ __forceinline__ double fmin_(double a, double b);
+  static __device__ __forceinline__ double fmax_(double a, double b);
   static constexpr double kTiny = 1e-290;     // below this a cube root argument is scaled
   static constexpr double kScaleUp = 0x1p300;  // 2^300
   static constexpr double kScaleDown = 0x1p-100; // its cube root, inverted
@@ -308,6 +308,37 @@ __device__ __forceinline__ bool zero64(double v) { return (uint64_t(__double_as_
 // a > b (a <= b) for non-negative finite a, b: their bit patterns order as integers
 __device__ __forceinline__ bool gt_pos(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
 __device__ __forceinline__ bool le_pos(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+// Order tests of arbitrary-sign doubles as integers: key(a) < key(b) iff a < b for non-NaN
+// a, b (-0 sorts just below +0).  Overloaded for float (plain compares on the FP32 pipe).
+__device__ __forceinline__ int64_t key64(double v) {
+  const int64_t b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool nan64(double v) {
+  return (uint64_t(__double_as_longlong(v)) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool cmp_lt(double a, double b) { return key64(a) < key64(b); }
+__device__ __forceinline__ bool cmp_le(double a, double b) { return key64(a) <= key64(b); }
+__device__ __forceinline__ bool cmp_lt(float a, float b) { return a < b; }
+__device__ __forceinline__ bool cmp_le(float a, float b) { return a <= b; }
+// v > 0 and v <= 0 from the sign and magnitude bits (a NaN with clear sign bit counts as > 0)
+__device__ __forceinline__ bool gt0(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool le0(double v) { return __double_as_longlong(v) <= 0; }
+__device__ __forceinline__ bool gt0(float v) { return v > 0.0f; }
+__device__ __forceinline__ bool le0(float v) { return v <= 0.0f; }
+// |d| < c for c >= 0
+__device__ __forceinline__ bool abs_lt(double d, double c) {
+  return (uint64_t(__double_as_longlong(d)) & 0x7fffffffffffffffull) < uint64_t(__double_as_longlong(c));
+}
+// fmin / fmax with their NaN rule (a NaN argument yields the other one), without the FP64 pipe
+__device__ __forceinline__ double fmin64(double a, double b) {
+  return (nan64(a) || (!nan64(b) && cmp_lt(b, a))) ? b : a;
+}
+__device__ __forceinline__ double fmax64(double a, double b) {
+  return (nan64(a) || (!nan64(b) && cmp_lt(a, b))) ? b : a;
+}
+__device__ __forceinline__ double Math<double>::fmin_(double a, double b) { return fmin64(a, b); }
+__device__ __forceinline__ double Math<double>::fmax_(double a, double b) { return fmax64(a, b); }
 
 __device__ __forceinline__ bool bad_inputs(double F, double K, double T, int flag) {
   // also rejects NaN and +-inf
@@ -385,7 +416,7 @@ __device__ __forceinline__ Quote classify_quote(double F, double K, double T, do
 // ln beta for a solved row; beta near or below the subnormal range takes it
 // from ln tv so that it keeps its relative accuracy
 __device__ __forceinline__ double log_beta(double beta, double F, double K, double T, double P, int flag) {
-  if (beta > 1e-290) return log_fp64(beta);
+  if (gt_pos(beta, 1e-290)) return log_fp64(beta);
   const Quote q = classify_quote(F, K, T, P, flag);
   return log_fp64(q.tv) + log_fp64(rsqrt(F * K));
 }
@@ -420,10 +451,10 @@ __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& n
   const R sc = M::sqrt_(R(2) * ax);
   const R e = M::erfcx_pos_(sc * R(kInvSqrt2)); // sc >= 0
   const R bc = R(0.5) * bmax * (R(1) - e);
-  const bool low = beta <= bc;
+  const bool low = cmp_le(beta, bc);
   const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
   const R su = sc + R(kSqrtPiOver2) * (R(1) + e);
-  const bool has_l = sl > R(0);
+  const bool has_l = gt0(sl);
   const R sn = low ? (has_l ? sl : R(1)) : su;
   const R h = x / sn, t = R(0.5) * sn;
   // both arguments are <= 0: h + t < 0 below s_c, -h - t < 0 above it, h - t < 0 always
@@ -437,8 +468,8 @@ __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& n
   nd.bn = (low && !has_l) ? R(0) : val;
   nd.bsn = bs;
   int region;
-  if (low) region = (beta < nd.bn) ? kLower : kMidLow;
-  else region = (beta <= bmax - val) ? kMidHigh : kUpper;
+  if (low) region = cmp_lt(beta, nd.bn) ? kLower : kMidLow;
+  else region = cmp_le(beta, bmax - val) ? kMidHigh : kUpper;
   nd.bb = (region == kUpper) ? betac : beta;
   return region;
 }
@@ -460,7 +491,7 @@ template <>
 __device__ __forceinline__ float neg_ncdfinv<float>(float G, bool) { return -::normcdfinvf(G); }
 template <>
 __device__ __forceinline__ double neg_ncdfinv<double>(double G, bool fast) {
-  if (fast && G >= 1e-37) {
+  if (fast && cmp_le(1e-37, G)) {
     const double y0 = double(::normcdfinvf(float(G))); // <= 0
     const double ey = exp_fp64(0.5 * y0 * y0);         // e^{y0^2/2} = 1 / (sqrt(2 pi) phi(y0))
     return -(fma(kSqrt2Pi * G, ey, -(kSqrtPiOver2 * erfcx_nonneg(-y0 * kInvSqrt2))) + y0);
@@ -489,9 +520,9 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       // u = (beta/kappa)^(1/3); below ~1e-290 the cube root of the argument scaled by 2^300 times
       // 2^-100 (exact scalings, no branch), and through ln beta only where beta/kappa underflowed
       const R v = beta * inv_kap;
-      const bool tiny = v < M::kTiny;
+      const bool tiny = cmp_lt(v, M::kTiny);
       R u = M::cbrt_(tiny ? v * M::kScaleUp : v) * (tiny ? M::kScaleDown : R(1));
-      if (__builtin_expect(!(v > R(0)), 0)) u = M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
+      if (__builtin_expect(!gt0(v), 0)) u = M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
       const R ul = M::cbrt_(bl * inv_kap);
       const R al = ax * R(kInvSqrt3) / sl;
       // Phi(-al) = phi(al) Y(-al) = exp(-al^2/2) erfcx(al/sqrt 2) / 2: one exponential shared with phi(al)
@@ -500,7 +531,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R dGl = R(3) * bl * (R(kInvSqrt2Pi) * eal) * al / (sl * ul * bsl);
       const R r = shape_monotone<R>(ul, R(0), Gl, R(1), dGl);
       const R G = M::fmin_(rational_cubic<R>(u, R(0), ul, R(0), Gl, R(1), dGl, r), R(0.5));
-      return ax * R(kInvSqrt3) / neg_ncdfinv<R>(G, kFastInv && double(beta) >= kDeepBeta);
+      return ax * R(kInvSqrt3) / neg_ncdfinv<R>(G, kFastInv && cmp_le(kDeepBeta, double(beta)));
     }
     case kMidLow: {
       // rational cubic in b on [b_l, b_c], zero curvature of s(b) at the inflection b_c
@@ -508,8 +539,9 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
       const R bc = R(0.5) * nd.bmax * (R(1) - e);
       const R bl = nd.bn;
-      const R d0 = (bl > R(0)) ? R(1) / nd.bsn : dc;
-      const R s0 = (bl > R(0)) ? sl : R(0);
+      const bool blp = gt0(bl);
+      const R d0 = blp ? R(1) / nd.bsn : dc;
+      const R s0 = blp ? sl : R(0);
       const R D = bc - bl;
       const R r = shape_zero_curv_right<R>(D, s0, sc, d0, dc);
       return rational_cubic<R>(nd.bb, bl, bc, s0, sc, d0, dc, r);
@@ -608,6 +640,15 @@ __device__ __forceinline__ R householder_step(R x, R beta, R lnbetac, R inv_lnbe
 // rounding moves s by ~1e-7 nu^2, below double rounding.  nu itself, the
 // residual, stays double.
 // ---------------------------------------------------------------------------
+// 1/s for an iterate s > 0.  Roots below 2^-1000 occur only at the money (x = 0, a time
+// value near or below the subnormal range), where h = x/s = 0 whatever s is and the other
+// products with 1/s carry a power of s that has already underflowed; there 1/s itself would
+// overflow (s subnormal) and turn h into 0 * inf.  The reciprocal is taken of max(s, 2^-1000),
+// the maximum by an integer compare of the bit patterns.
+__device__ __forceinline__ double inv_iterate(double s) {
+  return 1.0 / (le_pos(s, 0x1p-1000) ? 0x1p-1000 : s);
+}
+
 struct Last {
   double s;      // the iterate of the last evaluation
   double za, zb; // arguments of the two Mills ratios there
@@ -621,7 +662,7 @@ struct Last {
 template <bool kF32Ratios>
 __device__ __forceinline__ double step64(double x, double bmax, double beta, double lnbetac, double inv_lnbeta,
                                          int region, double s, Last& last) {
-  const double inv_s = 1.0 / s;
+  const double inv_s = inv_iterate(s);
   const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
   const double lbs = log_bs<double>(h, t);
   const bool taylor = region != kUpper && le_pos(t, kTaylorT) && le_pos(-x, kTaylorX);
@@ -638,7 +679,8 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   last.yb = yb;
   last.lbs = lbs;
   // 1/b_s where the middle objective or the larger ratio of the pair needs it
-  const bool need_ibs = region == kMidLow || region == kMidHigh || (region == kLower ? hpt > 0.0 : hpt <= 0.0);
+  const bool hpos = gt0(hpt);
+  const bool need_ibs = region == kMidLow || region == kMidHigh || (region == kLower ? hpos : !hpos);
   double ibs = need_ibs ? exp_fp64(-lbs) : 0.0;
   double E1 = bmax * ibs;
   double beta_ibs = beta * ibs;
@@ -651,11 +693,11 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   }
   double nu, L = 0.0, q = 0.0, iL = 0.0;
   if (region == kUpper) {
-    const double gam = (hpt > 0.0) ? ya + yb : (E1 - ya) + yb;
+    const double gam = hpos ? ya + yb : (E1 - ya) + yb;
     q = 1.0 / gam;
     nu = -(lnbetac - lbs - log_fp64(gam)) * gam;
   } else {
-    const double rho = taylor ? rho_taylor<double>(h, t) : (hpt <= 0.0 ? ya - yb : (E1 - ya) - yb);
+    const double rho = taylor ? rho_taylor<double>(h, t) : (!hpos ? ya - yb : (E1 - ya) - yb);
     if (region == kLower) {
       L = lbs + log_fp64(rho); // ln b
       // 1/rho and 1/L from one division: 1/rho = L / (rho L), 1/L = rho / (rho L)
@@ -717,7 +759,7 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
 // Also records 1/b_s at s (ibs) for adjoint_reuse.
 __device__ __forceinline__ double step64_final(double x, double bmax, double bb, int region, double s, float sf,
                                                float xf, Last& last) {
-  const double inv_s = 1.0 / s;
+  const double inv_s = inv_iterate(s);
   const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
   const double lbs = log_bs<double>(h, t);
   const bool taylor = region != kUpper && le_pos(t, kTaylorT) && le_pos(-x, kTaylorX);
@@ -737,10 +779,10 @@ __device__ __forceinline__ double step64_final(double x, double bmax, double bb,
   if (finite64(ibs)) {
     const double E1 = bmax * ibs;
     if (region == kUpper) {
-      const double gam = (hpt > 0.0) ? ya + yb : (E1 - ya) + yb;
+      const double gam = gt0(hpt) ? ya + yb : (E1 - ya) + yb;
       nu = gam - bb * ibs;
     } else {
-      const double rho = taylor ? rho_taylor<double>(h, t) : (hpt <= 0.0 ? ya - yb : (E1 - ya) - yb);
+      const double rho = taylor ? rho_taylor<double>(h, t) : (le0(hpt) ? ya - yb : (E1 - ya) - yb);
       nu = bb * ibs - rho;
     }
   } else {
@@ -936,17 +978,17 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
                                               double bmax, double inv_sqT, double rsq, double g, double tau, int mode,
                                               const Last& last) {
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-  const double inv_s = 1.0 / s;
+  const double inv_s = inv_iterate(s);
   const double h = x * inv_s, t = 0.5 * s, hpt = h + t;
   const double za = -fabs(hpt), zb = h - t;
   // the shift is used while the final step was small: |s - s_last| < 1e-5 s bounds the argument
   // moves by 1e-5 (|z| + s), so the neglected third-order term stays below ~1e-11 relative
-  const bool near = last.pair && fabs(s - last.s) < 1e-5 * s;
+  const bool near = last.pair && abs_lt(s - last.s, 1e-5 * s);
   const double ya = near ? mills_shift(last.ya, last.za, za - last.za) : mills_small(za);
   const double yb = near ? mills_shift(last.yb, last.zb, zb - last.zb) : mills_small(zb);
   const double lbs = log_bs<double>(h, t);
   double ibs;
-  if (__double_as_longlong(last.ibs) > 0 && fabs(lbs - last.lbs) < 1e-3) {
+  if (__double_as_longlong(last.ibs) > 0 && abs_lt(lbs - last.lbs, 1e-3)) {
     // 1/b_s from the last step's: exp(-d) to third order, d = lbs - last.lbs (|d| < 1e-3: d^4/24 < 5e-14)
     const double d = lbs - last.lbs;
     ibs = last.ibs * fma(fma(fma(d, -1.0 / 6.0, 0.5), d, -1.0), d, 1.0);
@@ -959,9 +1001,10 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
     E1 = kSqrt2Pi * exp_fp64(0.5 * hpt * hpt);
     E2 = kSqrt2Pi * exp_fp64(0.5 * zb * zb);
   }
-  const double y_hpt = hpt <= 0.0 ? ya : E1 - ya;  // Y(h + t)
-  const double y_mhpt = hpt <= 0.0 ? E1 - ya : ya; // Y(-h - t)
-  const bool call = flag > 0, fle = F <= K;
+  const bool hneg = le0(hpt);
+  const double y_hpt = hneg ? ya : E1 - ya;  // Y(h + t)
+  const double y_mhpt = hneg ? E1 - ya : ya; // Y(-h - t)
+  const bool call = flag > 0, fle = le_pos(F, K);
   const bool itm = call ? !fle : fle;
   const double y_tmh = itm ? E2 - yb : 0.0; // Y(t - h), in-the-money quotes only
   const double u1 = fle ? (call ? y_hpt : y_mhpt) : (call ? y_tmh : yb);  // Y(theta d1)
@@ -973,7 +1016,7 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   const double jK = sg * u2 * (F * rsq2) * inv_sqT;
   const double jT = -0.5 * sigma * inv_sqT * inv_sqT;
   Grad out;
-  const bool in_g = tau * jP < 1.0; // V > tau
+  const bool in_g = cmp_lt(tau * jP, 1.0); // V > tau
   if (mode == 0 || (mode <= 2 && in_g)) {
     out.dP = g * jP;
     out.dF = g * jF;
