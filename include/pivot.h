@@ -261,14 +261,16 @@ int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream);
  * exponential (fn = 1), which the solver uses for ln b, ln beta, 1/b_s and
  * the seeds (P. T. P. Tang's method; within 1 ulp), and (fn = 2) the
  * -Phi^{-1}(x) of the lower- and upper-region guesses (appendix stage 4),
- * x in (0, 1/2]: from 1e-37 on a float start and one FP64 Newton step
- * (relative error below ~1e-10), below it the library's normcdfinv; and
- * (fn = 3) 1/x by the solver's fast quotient (the hardware reciprocal estimate
- * refined by two Newton-Raphson steps, within 1 ulp, for normal x of
- * magnitude below 2^1021; the IEEE division elsewhere).
+ * x in (0, 1/2]: from 1e-37 on the float inverse normal CDF (seed accuracy,
+ * relative error ~1e-6), below it the library's FP64 normcdfinv; (fn = 3) 1/x
+ * by the solver's fast quotient (the hardware reciprocal estimate refined by
+ * two Newton-Raphson steps, within 1 ulp, for normal x of magnitude below
+ * 2^1021; the IEEE division elsewhere); and (fn = 4) the guesses' cube root
+ * (float cube root of the scaled mantissa, ~1e-7 relative, for positive
+ * normal x; the library's FP64 cbrt elsewhere).
  *   in : x (n float64)   out: y (n float64)
- * Exposed so that they can be checked on their own; fn outside {0, 1, 2, 3}
- * is PIVOT_E_OPTS.
+ * Exposed so that they can be checked on their own; fn outside 0..4 is
+ * PIVOT_E_OPTS.
  */
 int pivot_elementary(int32_t fn, int64_t n, const double* x, double* y, void* stream);
 

@@ -200,11 +200,12 @@ def mills_ratio(z):
 
 def elementary(fn: str, x):
     """The library's FP64 log (fn="log"), exp (fn="exp"), the guesses' -Phi^{-1} (fn="neg_ncdfinv",
-    x in (0, 1/2]) or the solver's fast reciprocal (fn="rcp"), evaluated by its kernel."""
+    x in (0, 1/2]), the solver's fast reciprocal (fn="rcp") or the guesses' cube root (fn="cbrt"),
+    evaluated by its kernel."""
     dev = _device_of(x)
     xx = _on(x, dev, torch.float64)
     y = torch.empty_like(xx)
-    _native.call("pivot_elementary", {"log": 0, "exp": 1, "neg_ncdfinv": 2, "rcp": 3}[fn], xx.numel(), _p(xx), _p(y), _stream(dev))
+    _native.call("pivot_elementary", {"log": 0, "exp": 1, "neg_ncdfinv": 2, "rcp": 3, "cbrt": 4}[fn], xx.numel(), _p(xx), _p(y), _stream(dev))
     return _host_result((x,), [y])[0]
 
 

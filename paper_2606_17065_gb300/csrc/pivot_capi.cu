@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(kBlock) k_elementary(int fn, int64_t n, const 
     y[i] = fn == 0   ? pivot::log_fp64(x[i])
            : fn == 1 ? pivot::exp_fp64(x[i])
            : fn == 2 ? pivot::neg_ncdfinv<double>(x[i], true)
-                     : pivot::div_fast(1.0, x[i]);
+           : fn == 3 ? pivot::div_fast(1.0, x[i])
+                     : pivot::Math<double>::cbrt_(x[i]);
 }
 
 __global__ void __launch_bounds__(kBlock) k_mills_ratio(int64_t n, const double* __restrict__ z,
@@ -774,7 +775,7 @@ int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream) {
 }
 
 int pivot_elementary(int32_t fn, int64_t n, const double* x, double* y, void* stream) {
-  if (fn < 0 || fn > 3) return PIVOT_E_OPTS;
+  if (fn < 0 || fn > 4) return PIVOT_E_OPTS;
   if (n < 0) return PIVOT_E_SIZE;
   if (n == 0) return PIVOT_OK;
   int dev = -1;

@@ -162,7 +162,21 @@ struct Math<double> {
   static __device__ __forceinline__ double exp_(double v) { return exp_fp64(v); }
   static __device__ __forceinline__ double log_(double v) { return log_fp64(v); }
   static __device__ __forceinline__ double sqrt_(double v) { return ::sqrt(v); }
-  static __device__ __forceinline__ double cbrt_(double v) { return ::cbrt(v); }
+  // the guesses' cube roots, to seed accuracy (~1e-7 relative, against the guess's ~1e-2
+  // interpolation error): v = m 2^(3q + r) with m in [1, 2), r in {0, 1, 2} from the exponent
+  // bits, the float cube root of m 2^r, and q added to its exponent as an integer; arguments
+  // outside the positive normal range take the library's FP64 cbrt
+  static __device__ __forceinline__ double cbrt_(double v) {
+    const int64_t b = __double_as_longlong(v);
+    if (!(b > 0x000fffffffffffffLL && b < 0x7ff0000000000000LL)) return ::cbrt(v);
+    const int e = int(b >> 52) - 1023;
+    const int q = (e >= 0 ? e : e - 2) / 3; // floor(e / 3)
+    const int r = e - 3 * q;
+    const float m = __int_as_float(0x3f800000 | int((b >> 29) & 0x7fffff)) * float(1 << r);
+    const uint32_t cb = __float_as_uint(::cbrtf(m)); // in [1, 2)
+    return __longlong_as_double(int64_t((uint64_t(((cb >> 23) & 0xff) - 127 + 1023 + q) << 52) |
+                                        (uint64_t(cb & 0x7fffff) << 29)));
+  }
   static __device__ __forceinline__ double ncdf_(double v) { return ::normcdf(v); }
   static __device__ __forceinline__ double fma_(double a, double b, double c) { return ::fma(a, b, c); }
   static __device__ __forceinline__ double fmin_(double a, double b);
@@ -502,14 +516,10 @@ __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& n
 
 // -Phi^{-1}(G) for the guesses, G in (0, 1/2].  In double, for G from 1e-37
 // on (the float range) and where `fast` (rows with beta >= kDeepBeta, whose
-// lower-region G stays above ~1e-35): a float start, within a few float ulps,
-// and one Newton step on Phi(y) = G in double,
-//   y1 = y0 - (Phi(y0) - G)/phi(y0) = y0 - (Y(y0) - sqrt(2 pi) G e^{y0^2/2}),
-// whose error ~ |y0| e0^2 / 2 (e0 ~ 1e-6 at y0 ~ -13) is below 1e-10; near
-// y = 0 the rounding of the difference leaves ~3e-16 absolute.  Both are far
-// below the guess's own interpolation error.  It runs on the table-driven erfcx and exp
-// rather than the general-purpose FP64 normcdfinv and its branches.  Other
-// arguments take the library function.
+// lower-region G stays above ~1e-35): the float inverse normal CDF, within a
+// few float ulps (relative error ~1e-6 in the guess), five orders of magnitude
+// below the guess's own interpolation error (~1e-2), which the FP64
+// Householder steps remove.  Other arguments take the library's FP64 function.
 constexpr double kDeepBeta = 1e-100;
 template <typename R>
 __device__ __forceinline__ R neg_ncdfinv(R G, bool fast);
@@ -517,11 +527,7 @@ template <>
 __device__ __forceinline__ float neg_ncdfinv<float>(float G, bool) { return -::normcdfinvf(G); }
 template <>
 __device__ __forceinline__ double neg_ncdfinv<double>(double G, bool fast) {
-  if (fast && cmp_le(1e-37, G)) {
-    const double y0 = double(::normcdfinvf(float(G))); // <= 0
-    const double ey = exp_fp64(0.5 * y0 * y0);         // e^{y0^2/2} = 1 / (sqrt(2 pi) phi(y0))
-    return -(fma(kSqrt2Pi * G, ey, -(kSqrtPiOver2 * erfcx_nonneg(-y0 * kInvSqrt2))) + y0);
-  }
+  if (fast && cmp_le(1e-37, G)) return -double(::normcdfinvf(float(G)));
   return -::normcdfinv(G);
 }
 

@@ -46,13 +46,13 @@ def test_argument_errors_before_any_device_access():
 
 def test_elementary_function_codes():
     """pivot_elementary takes fn 0 (log), 1 (exp), 2 (the guesses' -Phi^-1), 3 (the fast
-    reciprocal); any other code is
+    reciprocal), 4 (the guesses' cube root); any other code is
     PIVOT_E_OPTS, and an empty batch succeeds without touching the device."""
     lib = _native.lib()
     fake = ctypes.c_void_p(0x1000)
-    for fn in (-1, 4, 99):
+    for fn in (-1, 5, 99):
         assert lib.pivot_elementary(fn, 4, fake, fake, None) == 4
-    for fn in (0, 1, 2, 3):
+    for fn in (0, 1, 2, 3, 4):
         assert lib.pivot_elementary(fn, 0, None, None, None) == 0
         assert lib.pivot_elementary(fn, -1, fake, fake, None) == 1
 

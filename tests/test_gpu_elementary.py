@@ -53,8 +53,8 @@ def test_exp_fp64():
 
 
 def test_neg_ncdfinv_of_the_guesses():
-    """-Phi^{-1}(G) of the lower- and upper-region guesses: a float start and one FP64 Newton step
-    from 1e-37 on, the library's normcdfinv below; against 50-digit mpmath and scipy's ndtri."""
+    """-Phi^{-1}(G) of the lower- and upper-region guesses: the float inverse normal CDF from 1e-37
+    on (seed accuracy), the library's FP64 normcdfinv below; against 50-digit mpmath and scipy."""
     mp = pytest.importorskip("mpmath")
     special = pytest.importorskip("scipy.special")
     rng = np.random.default_rng(3)
@@ -66,17 +66,31 @@ def test_neg_ncdfinv_of_the_guesses():
         ref = np.array([float(mp.findroot(lambda y: mp.erfc(y / mp.sqrt(2)) / 2 - mp.mpf(float(g)), -special.ndtri(g)))
                         for g in G])
     err = np.abs(got - ref)
-    # Newton from a float start: ~1e-11 relative; near G = 1/2 (y -> 0) ~3e-16 absolute
-    assert np.all(err <= 1e-10 * np.abs(ref) + 1e-15), (err / np.maximum(np.abs(ref), 1e-300)).max()
+    # float branch: a few float ulps of y, plus the rounding of G to float near y = 0
+    assert np.all(err <= 2e-6 * np.abs(ref) + 1e-7), (err / np.maximum(np.abs(ref), 1e-300)).max()
     # the library branch below 1e-37 is FP64-accurate
     lo = G < 1e-37
     assert np.all(err[lo] <= 1e-14 * np.abs(ref[lo]))
-    assert got[G == 0.5][0] == 0.0 or abs(got[G == 0.5][0]) < 1e-15
+    assert abs(got[G == 0.5][0]) < 1e-7
     # dense sample against scipy
     g2 = np.exp(rng.uniform(np.log(1e-37), np.log(0.5), 200_000))
     got2 = to_np(api.elementary("neg_ncdfinv", to_dev(g2)))
     ref2 = -special.ndtri(g2)
-    assert np.all(np.abs(got2 - ref2) <= 1e-10 * np.abs(ref2) + 1e-15)
+    assert np.all(np.abs(got2 - ref2) <= 2e-6 * np.abs(ref2) + 1e-7)
+
+
+def test_seed_cube_root():
+    """The guesses' cube root: float cube root of the mantissa scaled into [1, 8), exponent added
+    as an integer, ~1e-7 relative over the whole positive normal range; library cbrt elsewhere."""
+    rng = np.random.default_rng(5)
+    v = np.concatenate([10.0 ** rng.uniform(-307.5, 308, 500_000), rng.uniform(0.5, 8.0, 100_000),
+                        [1.0, 8.0, 27.0, 2.0 ** -1022, 2.0 ** 1023, 0.125]])
+    got = to_np(api.elementary("cbrt", to_dev(v)))
+    ref = np.cbrt(v)
+    assert np.all(np.abs(got - ref) <= 2.5e-7 * ref)
+    special = np.array([0.0, 5e-324, 1e-310, np.inf])
+    got = to_np(api.elementary("cbrt", to_dev(special)))
+    assert np.allclose(got, np.cbrt(special), rtol=1e-15, atol=0)
 
 
 def test_fast_reciprocal():
