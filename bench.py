@@ -715,20 +715,19 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1) / max(args.steps // 2, 1)
 
-    # ---- end to end through the public API with pinned host buffers
+    # ---- end to end through the public API with pinned host buffers: inputs and the caller's
+    # outputs in pinned host memory, allocated once as a serving loop would (a first pinning of
+    # ~0.7 GB of outputs costs ~50 ms once and is not part of the steady state)
     hF, hK, hT, hP = (t.cpu().pin_memory() for t in (F, K, T, P))
     hflag = flag.cpu().pin_memory()
-    # warm-up in the timed loop's pattern (the previous result held during the next call), so
-    # that the pinned-memory cache holds both output sets before timing: the first call that
-    # needs the second set pins ~0.7 GB of host memory (~46 ms once)
-    res = None
-    for _ in range(3):
-        res = pv.iv_forward_backward(hF, hK, hT, hP, hflag, tau=TAU, gate=GATE)
+    hout = [torch.empty(n, dtype=d).pin_memory() for d in (torch.float64, torch.uint8) + (torch.float64,) * 4]
+    for _ in range(2):
+        pv.iv_forward_backward(hF, hK, hT, hP, hflag, tau=TAU, gate=GATE, out=hout)
     torch.cuda.synchronize()
     e2e_steps = max(min(args.steps, 5), 1)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        res = pv.iv_forward_backward(hF, hK, hT, hP, hflag, tau=TAU, gate=GATE)
+        res = pv.iv_forward_backward(hF, hK, hT, hP, hflag, tau=TAU, gate=GATE, out=hout)
         float(res[0][0])  # results are on the host
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(e2e_s, world)

@@ -113,14 +113,32 @@ def _pinned_outputs(n, dtypes):
     return [buf[o:o + n * torch.empty((), dtype=d).element_size()].view(d) for o, d in zip(offs, dtypes)]
 
 
-def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args):
+def _check_out(out, n, dtypes):
+    """Caller-provided host outputs: contiguous CPU tensors of n rows and the outputs' dtypes."""
+    if len(out) != len(dtypes):
+        raise ValueError(f"out must hold {len(dtypes)} tensors")
+    for t, d in zip(out, dtypes):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != d or t.numel() != n or not t.is_contiguous():
+            raise ValueError(f"out tensors must be contiguous host tensors of {n} rows, dtypes {dtypes}")
+    return list(out)
+
+
+def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args, out=None):
     """Run one row-wise entry point.  `build_args(m, ins, outs)` returns its
     arguments for m rows of device tensors, stream excluded.  Device inputs
     run in place on the current stream; host inputs larger than HOST_CHUNK are
     pipelined chunk by chunk (host -> device, kernel, device -> host on
-    rotating streams) into pinned host outputs."""
+    rotating streams) into pinned host outputs, the caller's (`out`, host
+    inputs only) or new ones."""
     n = next(t for t in inputs if t is not None)
     n = n.numel() if isinstance(n, torch.Tensor) else len(n)
+    if out is not None and not _is_host(inputs):
+        raise ValueError("out is for host inputs only")
+    if out is not None and n <= HOST_CHUNK:
+        res = _rows_call(name, inputs, in_dtypes, out_dtypes, build_args)
+        for o, r in zip(_check_out(out, n, out_dtypes), res):
+            o.copy_(r)
+        return list(out)
     if not _is_host(inputs) or n <= HOST_CHUNK:
         dev = _device_of(*inputs)
         ins = [_on(t, dev, d) for t, d in zip(inputs, in_dtypes)]
@@ -131,7 +149,7 @@ def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args):
     dev = _device_of()
     hins = [_host_tensor(t, d) for t, d in zip(inputs, in_dtypes)]
     _check_lengths(n, *hins)
-    houts = _pinned_outputs(n, out_dtypes)
+    houts = _check_out(out, n, out_dtypes) if out is not None else _pinned_outputs(n, out_dtypes)
     streams = _copy_streams(dev)
     bufs = [([None if h is None else torch.empty(HOST_CHUNK, dtype=h.dtype, device=dev) for h in hins],
              [torch.empty(HOST_CHUNK, dtype=d, device=dev) for d in out_dtypes]) for _ in streams]
@@ -315,15 +333,16 @@ def iv_backward(F, K, T, flag, sigma, gbar=None, *, tau: float = 1e-6, gate="nan
 
 
 def iv_forward_backward(F, K, T, P, flag, gbar=None, *, tau: float = 1e-6, gate="nan", mode="fp64",
-                        householder: int = 0, mlp=None, fallback: float = 0.0, counters=None):
-    """Forward and gated adjoint in one pass; returns (sigma, status, dP, dF, dK, dT)."""
+                        householder: int = 0, mlp=None, fallback: float = 0.0, counters=None, out=None):
+    """Forward and gated adjoint in one pass; returns (sigma, status, dP, dF, dK, dT).  With host
+    inputs, ``out`` may give the six host outputs (pinned memory for overlapped copies)."""
     o = _opts(mode, householder, mlp, fallback, counters)
     f64 = torch.float64
     gm = _gate(gate)
     outs = _rows_call("pivot_iv_forward_backward", (F, K, T, P, flag, gbar),
                       (f64, f64, f64, f64, torch.int8, f64), (f64, torch.uint8, f64, f64, f64, f64),
                       lambda m, i, u: (m, *[_p(t) for t in i], float(tau), gm, *[_p(t) for t in u],
-                                       ctypes.byref(o)))
+                                       ctypes.byref(o)), out=out)
     return tuple(outs)
 
 

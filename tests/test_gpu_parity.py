@@ -332,6 +332,27 @@ def test_host_chunked_pipeline_matches_device_path(monkeypatch, call):
         assert torch.equal(torch.nan_to_num(g.double(), nan=7.0), torch.nan_to_num(w.cpu().double(), nan=7.0))
 
 
+def test_host_outputs_given_by_the_caller(monkeypatch):
+    """iv_forward_backward(..., out=...) writes the caller's host tensors, chunked or not, with the
+    same bits as the device path; a wrong dtype or length is refused."""
+    from paper_2606_17065_gb300 import api
+    monkeypatch.setattr(api, "HOST_CHUNK", 4096)
+    for n in (1000, 3 * 4096 + 77):
+        b = workloads.stress_batch(n, seed=213)
+        arrays = [b.F, b.K, b.T, oracle_inputs(b), b.flag]
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in arrays]
+        out = [torch.empty(n, dtype=d).pin_memory() for d in (torch.float64, torch.uint8) + (torch.float64,) * 4]
+        got = pv.iv_forward_backward(*host, out=out)
+        assert all(g is o for g, o in zip(got, out))
+        want = pv.iv_forward_backward(*[h.to(DEV) for h in host])
+        for g, w in zip(got, want):
+            assert torch.equal(torch.nan_to_num(g.double(), nan=7.0), torch.nan_to_num(w.cpu().double(), nan=7.0))
+    with pytest.raises(ValueError):
+        pv.iv_forward_backward(*host, out=out[:5])
+    with pytest.raises(ValueError):
+        pv.iv_forward_backward(*[h.to(DEV) for h in host], out=out)
+
+
 def test_full_size_stress_sampled():
     """16M stress rows in the benchmark's launch configuration; sampled rows checked one by one."""
     b = workloads.stress_batch(workloads.STRESS_N, seed=2)
