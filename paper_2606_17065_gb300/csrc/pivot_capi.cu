@@ -262,8 +262,17 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
           a.sigma[i] = q.sigma;
           if (a.status) a.status[i] = uint8_t(q.status);
           if (kBackward) {
-            if (kBS) write_grad_bs(a, i, F, K, T, fl, q.sigma, rr, qq, s_er[r], s_ec[r]);
-            else write_grad(a, i, F, K, T, fl, q.sigma);
+            // outside the open price interval, or invalid: the degenerate gradient of its status
+            const double g = a.gbar ? a.gbar[i] : 1.0;
+            const double v = pivot::degenerate_grad(q.status <= 3 || pivot::nan64(g), g, a.mode).dP;
+            if (a.dP) a.dP[i] = v;
+            if (a.dF) a.dF[i] = v;
+            if (a.dK) a.dK[i] = v;
+            if (a.dT) a.dT[i] = v;
+            if (kBS) {
+              if (a.dr) a.dr[i] = v;
+              if (a.dq) a.dq[i] = v;
+            }
           }
         } else {
           solve = true;

@@ -927,7 +927,7 @@ __device__ __forceinline__ Grad degenerate_grad(bool invalid, double g, int mode
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
   double v = qnan;
   if (!invalid) {
-    if (mode == 1) v = (g == 0.0) ? 0.0 : qnan;
+    if (mode == 1) v = zero64(g) ? 0.0 : qnan;
     if (mode >= 2) v = 0.0;
   }
   Grad out;

@@ -40,16 +40,6 @@ struct Args {
 constexpr int kCountBin0 = 6;
 constexpr int kCountReject = 18;
 
-__device__ __forceinline__ void write_grad(const Args& a, int64_t i, double F, double K, double T, int fl,
-                                           double sig) {
-  const double g = a.gbar ? a.gbar[i] : 1.0;
-  const pivot::Grad d = pivot::gated_adjoint(F, K, T, fl, sig, g, a.tau, a.mode);
-  if (a.dP) a.dP[i] = d.dP;
-  if (a.dF) a.dF[i] = d.dF;
-  if (a.dK) a.dK[i] = d.dK;
-  if (a.dT) a.dT[i] = d.dT;
-}
-
 // Black-Scholes form: the gated adjoint of a finished row in xi coordinates
 __device__ __forceinline__ void write_grad_bs(const Args& a, int64_t i, double F, double K, double T, int fl,
                                               double sig, double r, double q, double er, double ec) {

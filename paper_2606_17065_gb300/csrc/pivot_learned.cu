@@ -135,7 +135,15 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
         if (q.status != 0) {
           a.sigma[i] = q.sigma;
           if (a.status) a.status[i] = uint8_t(q.status);
-          if (kBackward) write_grad(a, i, F, K, T, fl, q.sigma);
+          if (kBackward) {
+            // outside the open price interval, or invalid: the degenerate gradient of its status
+            const double g = a.gbar ? a.gbar[i] : 1.0;
+            const double v = pivot::degenerate_grad(q.status <= 3 || pivot::nan64(g), g, a.mode).dP;
+            if (a.dP) a.dP[i] = v;
+            if (a.dF) a.dF[i] = v;
+            if (a.dK) a.dK[i] = v;
+            if (a.dT) a.dT[i] = v;
+          }
         } else {
           solve = true;
           S.bb[r] = q.tv;
