@@ -252,7 +252,7 @@ int pivot_bs_iv_forward_backward(int64_t n, const double* S, const double* K, co
  * adjoint writes Delta/V (Eq. implicit_iv with F phi(d1) = K phi(d2)) and the
  * normalised Black function writes b/b_s (Section 2, Eq. app_normalized_black).
  *   in : z (n float64)   out: y (n float64)
- * Exposed so that the FP64 erfcx behind it can be checked on its own.
+ * Exposed so that the FP64 Mills-ratio table behind it can be checked on its own.
  */
 int pivot_mills_ratio(int64_t n, const double* z, double* y, void* stream);
 

@@ -49,44 +49,44 @@ enum Region : int { kLower = 0, kMidLow = 1, kMidHigh = 2, kUpper = 3 };
 // mixed path.  Math<R> maps each function to its CUDA precision variant.
 template <typename R>
 struct Math;
-// erfcx(a) = exp(a^2) erfc(a) in FP64 for the Mills ratios: degree-9
-// Chebyshev interpolants on 161 intervals of [0, 64) (coefficients written by
-// gen_erfcx_table.py, ~1 ulp), the asymptotic series
-// erfcx(a) ~ (1/(a sqrt pi)) sum_n (-1)^n (2n-1)!! / (2a^2)^n from 64 on (ten
-// terms, truncation < 1e-30 there), and erfcx(a) = 2 exp(a^2) - erfcx(-a) for
-// a < 0 with a^2 split exactly by an fma.  The interval is read off the bit
-// pattern of a (interval 0 = [0, 1/16), then 16 equal parts per binade up to
-// 64), so the table covers every Mills ratio of a normal-range price in one
-// branch (the series only serves iterates far outside it) and the FP64 pipe
-// sees one fma for the local variable and the Horner chain; the table rows are
-// 96 bytes and hit L1.
-#include "erfcx_table.inc"
+// The Mills ratio M(w) = Y(-w) = Phi(-w)/phi(w) = sqrt(pi/2) erfcx(w/sqrt 2),
+// w >= 0, in FP64: degree-9 Chebyshev interpolants on 177 intervals of [0, 128)
+// (coefficients written by gen_mills_table.py, ~1 ulp) and the asymptotic series
+// M(w) ~ (1/w) sum_n (-1)^n (2n-1)!! / w^(2n) from 128 on (nine terms, truncation
+// below 1e-27 there).  Every Mills ratio the solver and the adjoint evaluate is
+// Y at a non-positive argument, i.e. M of its negation, so the table takes w
+// itself: no scaling of the argument or of the result.  The interval is read
+// off the bit pattern of w (interval 0 = [0, 1/16), then 16 equal parts per
+// binade up to 128), so the table covers every Mills ratio of a normal-range
+// price in one branch (the series only serves iterates far outside it) and the
+// FP64 pipe sees one fma for the local variable and the Horner chain; the
+// table rows are 96 bytes and hit L1.
+#include "mills_table.inc"
 
-__device__ __forceinline__ double erfcx_nonneg(double a) {
-  const uint64_t bits = uint64_t(__double_as_longlong(a)) & 0x7fffffffffffffffull; // a = -0 too
-  if (bits < 0x4050000000000000ull) { // |a| < 64
+__device__ __forceinline__ double mills_neg(double w) {
+  const uint64_t bits = uint64_t(__double_as_longlong(w)) & 0x7fffffffffffffffull; // w = -0 too
+  if (bits < 0x4060000000000000ull) { // |w| < 128
     // biased exponent and top four mantissa bits, less those of 1/16, plus one (0 below 1/16)
     const int k = max(int(bits >> 48) - ((1023 - 4) << 4) + 1, 0);
-    const double* c = kErfcxCoef[k];
-    const double tau = fma(a, __ldg(c + 10), __ldg(c + 11)); // in [-1, 1]; scale 2^j, offset an integer
+    const double* c = kMillsCoef[k];
+    const double tau = fma(w, __ldg(c + 10), __ldg(c + 11)); // in [-1, 1]; scale 2^j, offset an integer
     double v = __ldg(c + 9);
 #pragma unroll
     for (int j = 8; j >= 0; --j) v = fma(v, tau, __ldg(c + j));
     return v;
   }
-  const double ia = 1.0 / a;
-  const double w = 0.5 * ia * ia;
-  double s = -34459425.0;
-  s = fma(s, w, 2027025.0);
-  s = fma(s, w, -135135.0);
-  s = fma(s, w, 10395.0);
-  s = fma(s, w, -945.0);
-  s = fma(s, w, 105.0);
-  s = fma(s, w, -15.0);
-  s = fma(s, w, 3.0);
-  s = fma(s, w, -1.0);
-  s = fma(s, w, 1.0);
-  return s * ia * 0.564189583547756286948; // 1/sqrt(pi)
+  const double iw = 1.0 / w;
+  const double q = iw * iw;
+  double s = 2027025.0;
+  s = fma(s, q, -135135.0);
+  s = fma(s, q, 10395.0);
+  s = fma(s, q, -945.0);
+  s = fma(s, q, 105.0);
+  s = fma(s, q, -15.0);
+  s = fma(s, q, 3.0);
+  s = fma(s, q, -1.0);
+  s = fma(s, q, 1.0);
+  return s * iw;
 }
 
 // Table-driven FP64 logarithm and exponential (P. T. P. Tang's method, ACM TOMS
@@ -145,20 +145,19 @@ __device__ __forceinline__ double exp_fp64(double v) {
   return __longlong_as_double(__double_as_longlong(res) + (int64_t(n >> 7) << 52));
 }
 
-__device__ __forceinline__ double erfcx_fp64(double a) {
-  double r = erfcx_nonneg(fabs(a));
-  if (a < 0.0) {
-    const double p = a * a, e = fma(a, a, -p); // a^2 = p + e exactly
-    const double ex = 2.0 * exp_fp64(p);
-    r = (p < 709.0) ? fma(ex, e, ex) - r : INFINITY;
-  }
-  return r;
+// Y(z) = Phi(z)/phi(z) for any z: M(-z) for z <= 0, and for z > 0 the reflection
+// Y(z) = 1/phi(z) - Y(-z) = sqrt(2 pi) e^{z^2/2} - M(z), with z^2 split exactly by an fma
+__device__ __forceinline__ double mills_fp64(double z) {
+  if (__double_as_longlong(z) <= 0) return mills_neg(-z); // z <= 0 (and -0)
+  const double p = z * z, e = fma(z, z, -p);              // z^2 = p + e exactly
+  const double ex = kSqrt2Pi * exp_fp64(0.5 * p);
+  return !(p >= 1418.0) ? fma(ex, 0.5 * e, ex) - mills_neg(z) : INFINITY; // NaN stays NaN
 }
 
 template <>
 struct Math<double> {
-  static __device__ __forceinline__ double erfcx_(double v) { return erfcx_fp64(v); }
-  static __device__ __forceinline__ double erfcx_pos_(double v) { return erfcx_nonneg(v); } // v >= 0
+  // erfcx(v / sqrt 2) = sqrt(2/pi) M(v) for v >= 0
+  static __device__ __forceinline__ double erfcx_half_(double v) { return 0.797884560802865355880 * mills_neg(v); }
   static __device__ __forceinline__ double exp_(double v) { return exp_fp64(v); }
   static __device__ __forceinline__ double log_(double v) { return log_fp64(v); }
   static __device__ __forceinline__ double sqrt_(double v) { return ::sqrt(v); }
@@ -188,7 +187,7 @@ struct Math<double> {
 template <>
 struct Math<float> {
   static __device__ __forceinline__ float erfcx_(float v) { return ::erfcxf(v); }
-  static __device__ __forceinline__ float erfcx_pos_(float v) { return ::erfcxf(v); }
+  static __device__ __forceinline__ float erfcx_half_(float v) { return ::erfcxf(v * float(kInvSqrt2)); }
   static __device__ __forceinline__ float exp_(float v) { return ::expf(v); }
   static __device__ __forceinline__ float log_(float v) { return ::logf(v); }
   static __device__ __forceinline__ float sqrt_(float v) { return ::sqrtf(v); }
@@ -230,13 +229,15 @@ __device__ __forceinline__ float quot(float a, float d) { return a / d; }
 
 // Y(z) = Phi(z)/phi(z).  Kept out of line: it is called from many sites and
 // one shared copy keeps the kernels' instruction footprint small.
+static __device__ __noinline__ double mills_any(double z) { return mills_fp64(z); }
+static __device__ __noinline__ float mills_any(float z) { return float(kSqrtPiOver2) * ::erfcxf(-z * float(kInvSqrt2)); }
 template <typename R>
-__device__ __noinline__ R mills_y(R z) {
-  return R(kSqrtPiOver2) * Math<R>::erfcx_(-z * R(kInvSqrt2));
+__device__ __forceinline__ R mills_y(R z) {
+  return mills_any(z);
 }
 
-// Y(z) for z <= 0: no reflection branch
-static __device__ __noinline__ double mills_small(double z) { return kSqrtPiOver2 * erfcx_nonneg(-z * kInvSqrt2); }
+// Y(z) for z <= 0: the table at -z, no reflection branch
+static __device__ __noinline__ double mills_small(double z) { return mills_neg(-z); }
 // ... in either precision (the float path keeps mills_y)
 template <typename R>
 __device__ __forceinline__ R mills_nonpos(R z);
@@ -489,7 +490,7 @@ __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& n
   using M = Math<R>;
   const R ax = -x;
   const R sc = M::sqrt_(R(2) * ax);
-  const R e = M::erfcx_pos_(sc * R(kInvSqrt2)); // sc >= 0
+  const R e = M::erfcx_half_(sc); // erfcx(sqrt|x|), sc >= 0
   const R bc = R(0.5) * bmax * (R(1) - e);
   const bool low = cmp_le(beta, bc);
   const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
@@ -559,7 +560,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R al = quot(ax * R(kInvSqrt3), sl);
       // Phi(-al) = phi(al) Y(-al) = exp(-al^2/2) erfcx(al/sqrt 2) / 2: one exponential shared with phi(al)
       const R eal = M::exp_(R(-0.5) * al * al);
-      const R Gl = R(0.5) * eal * M::erfcx_pos_(al * R(kInvSqrt2));
+      const R Gl = R(0.5) * eal * M::erfcx_half_(al);
       const R dGl = quot(R(3) * bl * (R(kInvSqrt2Pi) * eal) * al, sl * ul * bsl);
       const R r = shape_monotone<R>(ul, R(0), Gl, R(1), dGl);
       const R G = M::fmin_(rational_cubic<R>(u, R(0), ul, R(0), Gl, R(1), dGl, r), R(0.5));
@@ -596,7 +597,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R uu = R(0.5) * nd.bn;
       // Phi(-su/2) and phi(su/2) from one exponential, as in the lower region
       const R esu = M::exp_(R(-0.125) * su * su);
-      const R vu = R(0.5) * esu * M::erfcx_pos_(su * R(0.5 * kInvSqrt2));
+      const R vu = R(0.5) * esu * M::erfcx_half_(R(0.5) * su);
       const R dvu = quot(R(kInvSqrt2Pi) * esu, nd.bsn);
       const R r = shape_monotone<R>(uu, R(0), vu, R(1), dvu);
       const R v = M::fmin_(rational_cubic<R>(R(0.5) * nd.bb, R(0), uu, R(0), vu, R(1), dvu, r), R(0.5));

@@ -437,15 +437,15 @@ def test_full_size_mixed_sampled():
     torch.cuda.empty_cache()
 
 
-def test_mills_ratio_fp64_erfcx():
-    """The library's FP64 erfcx (table + asymptotic series + reflection) through Y = Phi/phi,
-    against the oracle's quadrature Mills ratio."""
-    # the table's interval ends in a = -z/sqrt 2 (0, 1/16, then 16 parts per binade up to 64), each with
-    # its neighbours, and the switch to the asymptotic series at a = 64
-    ends = np.concatenate([[2.0 ** e * (1 + m / 16) for e in range(-4, 6) for m in range(16)], [64.0]])
-    z_ends = -np.sqrt(2.0) * np.concatenate([ends, np.nextafter(ends, 0), np.nextafter(ends, np.inf)])
+def test_mills_ratio_fp64_table():
+    """The library's FP64 Mills ratio (table in w = -z, asymptotic series, reflection for z > 0)
+    through Y = Phi/phi, against the oracle's quadrature Mills ratio."""
+    # the table's interval ends in w = -z (0, 1/16, then 16 parts per binade up to 128), each with
+    # its neighbours, and the switch to the asymptotic series at w = 128
+    ends = np.concatenate([[2.0 ** e * (1 + m / 16) for e in range(-4, 7) for m in range(16)], [128.0]])
+    z_ends = -np.concatenate([ends, np.nextafter(ends, 0), np.nextafter(ends, np.inf)])
     z = np.concatenate([np.linspace(-37.0, 37.0, 20001), -np.logspace(-12, 3, 400), np.logspace(-12, 1.5, 400),
-                        np.linspace(-100.0, -80.0, 2001), z_ends, [0.0, -0.0, np.inf, -np.inf]])
+                        np.linspace(-140.0, -120.0, 2001), z_ends, [0.0, -0.0, np.inf, -np.inf]])
     y = to_np(pv.api.mills_ratio(to_dev(z)))
     ref = np.array([oracle.mills(v) for v in z])
     fin = np.isfinite(ref) & (ref > 0)
