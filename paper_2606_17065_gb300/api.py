@@ -77,9 +77,28 @@ def _host_result(inputs, outs):
 # chunks of this size on three CUDA streams, so that the host-to-device copy of
 # one chunk, the kernels of the next and the device-to-host copy of a third
 # overlap.
-HOST_CHUNK = 1 << 20
+HOST_CHUNK = 1 << 22
 HOST_STREAMS = 3
+# The first and last chunk are split into halving pieces (1/8, 1/8, 1/4, 1/2 and back), so that
+# the first kernel starts after a short copy and the last copy back is short.
+HOST_RAMP = True
 _streams = {}
+
+
+def _chunks(n):
+    """(start, rows) of the chunks of an n-row host call."""
+    C = HOST_CHUNK
+    sizes = [min(C, n - lo) for lo in range(0, n, C)]
+    if HOST_RAMP and len(sizes) >= 3 and C >= 64:
+        head = [C // 8, C // 8, C // 4, C - C // 8 - C // 8 - C // 4]
+        last = sizes[-1]
+        tail = [last - last // 2 - last // 4 - last // 8, last // 8, last // 4, last // 2][::-1]
+        sizes = head + sizes[1:-1] + [m for m in tail if m > 0]
+    out, lo = [], 0
+    for m in sizes:
+        out.append((lo, m))
+        lo += m
+    return out
 
 
 def _copy_streams(device):
@@ -156,8 +175,7 @@ def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args, out=None):
     main = torch.cuda.current_stream(dev)
     for st in streams:
         st.wait_stream(main)
-    for k, lo in enumerate(range(0, n, HOST_CHUNK)):
-        m = min(HOST_CHUNK, n - lo)
+    for k, (lo, m) in enumerate(_chunks(n)):
         st = streams[k % len(streams)]
         dins, douts = bufs[k % len(streams)]
         with torch.cuda.stream(st):

@@ -161,6 +161,9 @@ struct Math<double> {
   static __device__ __forceinline__ double exp_(double v) { return exp_fp64(v); }
   static __device__ __forceinline__ double log_(double v) { return log_fp64(v); }
   static __device__ __forceinline__ double sqrt_(double v) { return ::sqrt(v); }
+  // the LBR node's s_c = sqrt(2|x|), which only places the guess's interpolation nodes: the float
+  // square root (relative error ~6e-8, against the guess's ~1e-2 interpolation error)
+  static __device__ __forceinline__ double sqrt_node_(double v) { return double(::sqrtf(float(v))); }
   // the guesses' cube roots, to seed accuracy (~1e-7 relative, against the guess's ~1e-2
   // interpolation error): v = m 2^(3q + r) with m in [1, 2), r in {0, 1, 2} from the exponent
   // bits, the float cube root of m 2^r, and q added to its exponent as an integer; arguments
@@ -191,6 +194,7 @@ struct Math<float> {
   static __device__ __forceinline__ float exp_(float v) { return ::expf(v); }
   static __device__ __forceinline__ float log_(float v) { return ::logf(v); }
   static __device__ __forceinline__ float sqrt_(float v) { return ::sqrtf(v); }
+  static __device__ __forceinline__ float sqrt_node_(float v) { return ::sqrtf(v); }
   static __device__ __forceinline__ float cbrt_(float v) { return ::cbrtf(v); }
   static __device__ __forceinline__ float ncdf_(float v) { return ::normcdff(v); }
   static __device__ __forceinline__ float fma_(float a, float b, float c) { return ::fmaf(a, b, c); }
@@ -489,7 +493,7 @@ template <typename R>
 __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& nd) {
   using M = Math<R>;
   const R ax = -x;
-  const R sc = M::sqrt_(R(2) * ax);
+  const R sc = M::sqrt_node_(R(2) * ax);
   const R e = M::erfcx_half_(sc); // erfcx(sqrt|x|), sc >= 0
   const R bc = R(0.5) * bmax * (R(1) - e);
   const bool low = cmp_le(beta, bc);
@@ -540,7 +544,7 @@ template <typename R, bool kFastInv = true>
 __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbeta) {
   using M = Math<R>;
   const R x = nd.x, ax = -x;
-  const R sc = M::sqrt_(R(2) * ax);
+  const R sc = M::sqrt_node_(R(2) * ax);
   const R e = nd.e;
   switch (region) {
     case kLower: {

@@ -1,0 +1,27 @@
+"""The host path's chunk schedule (api._chunks): contiguous, covering, bounded, ramped."""
+import pytest
+
+from paper_2606_17065_gb300 import api
+
+
+@pytest.mark.parametrize("n", [1, 255, 4096, 3 * 4096 + 77, 1 << 20, (1 << 21) + 5, 16777216, 5 * (1 << 21) - 3])
+@pytest.mark.parametrize("ramp", [False, True])
+def test_chunks_cover_rows_in_order(monkeypatch, n, ramp):
+    monkeypatch.setattr(api, "HOST_RAMP", ramp)
+    chunks = api._chunks(n)
+    lo = 0
+    for start, m in chunks:
+        assert start == lo and 0 < m <= api.HOST_CHUNK
+        lo += m
+    assert lo == n
+
+
+def test_ramp_halves_the_first_and_last_chunk(monkeypatch):
+    monkeypatch.setattr(api, "HOST_RAMP", True)
+    C = api.HOST_CHUNK
+    sizes = [m for _, m in api._chunks(8 * C)]
+    assert sizes[:4] == [C // 8, C // 8, C // 4, C // 2]
+    assert sizes[-4:] == [C // 2, C // 4, C // 8, C // 8]
+    assert sizes[4:-4] == [C] * 6
+    monkeypatch.setattr(api, "HOST_RAMP", False)
+    assert [m for _, m in api._chunks(8 * C)] == [C] * 8
