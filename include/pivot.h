@@ -371,7 +371,7 @@ int pivot_probe_stream(int32_t width, int64_t n, const double* F, const double* 
 /* Human-readable text for a return code. */
 const char* pivot_error_string(int code);
 
-/* ABI version (major * 10000 + minor * 100 + patch). */
+/* ABI version (major * 10000 + minor * 100 + patch).  200: pivot_opts gained `counters`. */
 int pivot_version(void);
 
 #ifdef __cplusplus

@@ -24,6 +24,7 @@ class PivotOpts(ctypes.Structure):
 
 
 COUNTERS_LEN = 24
+ABI_VERSION = 200  # the pivot_opts layout above
 
 
 _SIGNATURES = {
@@ -85,6 +86,8 @@ def lib():
             fn.restype = ctypes.c_int
         handle.pivot_error_string.restype = ctypes.c_char_p
         handle.pivot_mlp_trainer_bytes.restype = ctypes.c_int64
+        if handle.pivot_version() < ABI_VERSION:
+            raise RuntimeError(f"{LIB_PATH} is ABI {handle.pivot_version()}, this binding needs {ABI_VERSION}: rebuild it")
         _lib = handle
         return _lib
 

@@ -813,6 +813,6 @@ const char* pivot_error_string(int code) {
   return "unknown error";
 }
 
-int pivot_version(void) { return 100; }
+int pivot_version(void) { return 200; }
 
 }  // extern "C"
