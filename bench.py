@@ -44,22 +44,22 @@ BYTES_PER_ROW = 33 + 41
 # over one launch of 4,194,304 stress rows, divided by the rows), see
 # profiles/k_iv_binned_fwdbwd_stress.md.  Counts scale with the rows: every
 # launch of the same distribution does the same work per row on average.
-FLOPS_PER_ROW = 338.7
+FLOPS_PER_ROW = 323.0
 # dram__bytes_read.sum + dram__bytes_write.sum per row from the same capture.
-TRAFFIC_PER_ROW = 101.5
+TRAFFIC_PER_ROW = 101.6
 # Executed FLOPs per row of the other measured forms, counted by ncu the same way on one launch
 # of 4,194,304 rows of each workload (python bench.py --case <name> --rows 4194304; FP32 from
 # smsp__sass_thread_inst_executed_op_{fadd,fmul}_pred_on + 2 x ..._ffma_pred_on), see
 # profiles/flops_per_row_all_forms.md.
 FLOPS = {
     # case: (FP64 FLOP / row, FP32 FLOP / row)
-    "stress": (FLOPS_PER_ROW, 13.7),
-    "stress-mixed": (115.9, 231.7),
-    "body": (720.0, 15.5),
-    "body-mixed": (270.6, 508.9),
-    "body-learned": (269.8, 1589.0),
-    "bs-wide": (440.7, 16.8),
-    "bs-wide-mixed": (182.4, 271.7),
+    "stress": (FLOPS_PER_ROW, 18.7),
+    "stress-mixed": (114.2, 231.7),
+    "body": (682.7, 27.3),
+    "body-mixed": (266.5, 508.9),
+    "body-learned": (265.8, 1589.0),
+    "bs-wide": (422.6, 22.6),
+    "bs-wide-mixed": (180.4, 271.7),
 }
 # MLP inference of the learned seed, 2 -> 64 -> 64 -> 64 -> 1: 2 (2 64 + 64 64 + 64 64 + 64) FLOP
 # per seeded row on the BF16 tensor cores (algorithmic count)
