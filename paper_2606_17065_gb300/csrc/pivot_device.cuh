@@ -30,6 +30,7 @@ constexpr double kSqrt2Pi = 2.50662827463100050242;    // sqrt(2 pi)
 constexpr double kInvSqrt2Pi = 0.398942280401432677940; // 1/sqrt(2 pi)
 constexpr double kSqrtPiOver2 = 1.25331413731550025121; // sqrt(pi/2)
 constexpr double kInvSqrt2 = 0.707106781186547524401;
+constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr double kLnSqrt2Pi = 0.918938533204672741780;
 constexpr double kInvSqrt3 = 0.577350269189625764509;
 constexpr double kTwoPiOver3Sqrt3 = 1.20919957615614523543; // 2 pi / (3 sqrt 3)
@@ -467,6 +468,92 @@ __device__ __forceinline__ double log_beta(double beta, double F, double K, doub
 }
 
 // ---------------------------------------------------------------------------
+// The LBR node as functions of u = |x| alone (appendix stage 4): with
+// w = sqrt(u), e = erfcx(w), s_l = s_c - sqrt(pi/2)(1 - e) and
+// s_u = s_c + sqrt(pi/2)(1 + e), the node values scale with b_max:
+//   b_l = b_max u FL(w), b_s(s_l) = b_max GL(w), b_max - b_u = b_max FU(w),
+//   b_s(s_u) = b_max GU(w), s_l = u SL(w)
+// (node_table.inc, degree-6 Chebyshev pieces in float on 97 intervals of
+// [0, 64) indexed by the bit pattern of w, generated with mpmath by
+// gen_node_table.py, ~1e-7 relative).  The node only places the guess's
+// interpolation nodes and the region tests, so float precision is far below
+// the guess's own interpolation error; SL keeps s_l's relative accuracy where
+// s_c - sqrt(pi/2)(1 - e) would cancel (u -> 0).  u >= 4096 (|F/K| beyond
+// e^4096) takes the evaluated node.
+// ---------------------------------------------------------------------------
+#include "node_table.inc"
+
+constexpr int kNodeDeg = 6;
+constexpr float kNodeMaxU = 4096.0f;
+
+// a non-negative double below 2^128 as a float by its bits (mantissa truncated; values
+// below the float normal range give 0): integer instructions only
+__device__ __forceinline__ float pos_to_float(double v) {
+  const uint64_t b = uint64_t(__double_as_longlong(v));
+  const int ef = int(b >> 52) - 1023 + 127;
+  if (ef <= 0) return 0.0f;
+  return __uint_as_float((uint32_t(ef) << 23) | uint32_t((b >> 29) & 0x7fffff));
+}
+// a positive normal float (or 0) as a double by its bits: integer instructions only
+__device__ __forceinline__ double pos_to_double(float f) {
+  const uint32_t b = __float_as_uint(f);
+  if (b == 0u) return 0.0;
+  return __longlong_as_double(int64_t((uint64_t((b >> 23) - 127 + 1023) << 52) | (uint64_t(b & 0x7fffff) << 29)));
+}
+template <typename R>
+__device__ __forceinline__ R from_float(float f);
+template <>
+__device__ __forceinline__ double from_float<double>(float f) { return pos_to_double(f); }
+template <>
+__device__ __forceinline__ float from_float<float>(float f) { return f; }
+template <typename R>
+__device__ __forceinline__ float to_float(R v);
+template <>
+__device__ __forceinline__ float to_float<double>(double v) { return pos_to_float(v); }
+template <>
+__device__ __forceinline__ float to_float<float>(float v) { return v; }
+
+struct NodeTab {
+  float w, e, sl_u, fl_u, gl, fu, gu;
+};
+
+__device__ __forceinline__ float node_poly(const float* c, float tau) {
+  float v = __ldg(c + kNodeDeg);
+#pragma unroll
+  for (int j = kNodeDeg - 1; j >= 0; --j) v = fmaf(v, tau, __ldg(c + j));
+  return v;
+}
+
+// the node functions at u (float, 0 <= u < kNodeMaxU)
+__device__ __forceinline__ NodeTab node_tab(float u) {
+  NodeTab t;
+  t.w = sqrtf(u);
+  const uint32_t bits = __float_as_uint(t.w);
+  // biased exponent and top three mantissa bits, less those of 1/64, plus one (0 below 1/64)
+  const int k = max(int(bits >> 20) - ((127 - 6) << 3) + 1, 0);
+  const float* c = kNodeCoef[k];
+  const float tau = fmaf(t.w, __ldg(c), __ldg(c + 1));
+  c += 2;
+  t.e = node_poly(c, tau);
+  t.sl_u = node_poly(c + (kNodeDeg + 1), tau);
+  t.fl_u = node_poly(c + 2 * (kNodeDeg + 1), tau);
+  t.gl = node_poly(c + 3 * (kNodeDeg + 1), tau);
+  t.fu = node_poly(c + 4 * (kNodeDeg + 1), tau);
+  t.gu = node_poly(c + 5 * (kNodeDeg + 1), tau);
+  return t;
+}
+
+// s_l = u SL(w) alone (the guesses)
+__device__ __forceinline__ float node_sl_u(float u, float& w) {
+  w = sqrtf(u);
+  const uint32_t bits = __float_as_uint(w);
+  const int k = max(int(bits >> 20) - ((127 - 6) << 3) + 1, 0);
+  const float* c = kNodeCoef[k];
+  const float tau = fmaf(w, __ldg(c), __ldg(c + 1));
+  return node_poly(c + 2 + (kNodeDeg + 1), tau);
+}
+
+// ---------------------------------------------------------------------------
 // LBR boundary, region and rational initial guess (appendix stage 4).
 // The boundary is the inflection point s_c = sqrt(2|x|) of b(x, .) and the
 // two points s_l, s_u where its tangent there reaches 0 and b_max.  In closed
@@ -493,6 +580,24 @@ template <typename R>
 __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& nd) {
   using M = Math<R>;
   const R ax = -x;
+  const float uf = to_float<R>(ax);
+  if (uf < kNodeMaxU) {
+    // the tabulated node: b_c, and b_l, b_s(s_l) or b_max - b_u, b_s(s_u), all times b_max
+    const NodeTab tb = node_tab(uf);
+    const R e = from_float<R>(tb.e);
+    const R bc = R(0.5) * bmax * (R(1) - e);
+    const bool low = cmp_le(beta, bc);
+    nd.x = x;
+    nd.bmax = bmax;
+    nd.e = e;
+    nd.bn = bmax * (low ? ax * from_float<R>(tb.fl_u) : from_float<R>(tb.fu));
+    nd.bsn = bmax * from_float<R>(low ? tb.gl : tb.gu);
+    int region;
+    if (low) region = cmp_lt(beta, nd.bn) ? kLower : kMidLow;
+    else region = cmp_le(beta, bmax - nd.bn) ? kMidHigh : kUpper;
+    nd.bb = (region == kUpper) ? betac : beta;
+    return region;
+  }
   const R sc = M::sqrt_node_(R(2) * ax);
   const R e = M::erfcx_half_(sc); // erfcx(sqrt|x|), sc >= 0
   const R bc = R(0.5) * bmax * (R(1) - e);
@@ -540,18 +645,34 @@ __device__ __forceinline__ double neg_ncdfinv<double>(double G, bool fast) {
 // lnbeta is ln beta (lower region only).
 // kFastInv: -Phi^{-1} by neg_ncdfinv's float start and Newton step where it applies (else the
 // library function throughout)
+// s_c and (for the sides below the inflection) s_l of a row's node: from the node table
+// while |x| < 4096, where s_l = |x| SL keeps its relative accuracy as |x| -> 0
+template <typename R>
+__device__ __forceinline__ R node_sc(R ax, float uf) {
+  return uf < kNodeMaxU ? R(kSqrt2) * from_float<R>(sqrtf(uf)) : Math<R>::sqrt_node_(R(2) * ax);
+}
+template <typename R>
+__device__ __forceinline__ R node_sl(R ax, float uf, R sc, R e) {
+  if (uf < kNodeMaxU) {
+    float w;
+    return ax * from_float<R>(node_sl_u(uf, w));
+  }
+  return sc - R(kSqrtPiOver2) * (R(1) - e);
+}
+
 template <typename R, bool kFastInv = true>
 __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbeta) {
   using M = Math<R>;
   const R x = nd.x, ax = -x;
-  const R sc = M::sqrt_node_(R(2) * ax);
+  const float uf = to_float<R>(ax);
+  const R sc = node_sc<R>(ax, uf);
   const R e = nd.e;
   switch (region) {
     case kLower: {
       // lower tail: b ~ kappa Phi(-|x|/(sqrt3 s))^3 as s -> 0, kappa = 2 pi |x| / (3 sqrt 3).
       // Interpolate G = Phi(-|x|/(sqrt3 s)) against u = (beta/kappa)^(1/3) on [0, u_l]
       // (G(0) = 0, G'(0) = 1, G(u_l), G'(u_l) exact), then invert G for s.
-      const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
+      const R sl = node_sl<R>(ax, uf, sc, e);
       const R bl = nd.bn, bsl = nd.bsn, beta = nd.bb;
       const R kap = R(kTwoPiOver3Sqrt3) * ax, inv_kap = quot(R(1), kap);
       // u = (beta/kappa)^(1/3); below ~1e-290 the cube root of the argument scaled by 2^300 times
@@ -573,7 +694,7 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
     case kMidLow: {
       // rational cubic in b on [b_l, b_c], zero curvature of s(b) at the inflection b_c
       const R dc = quot(R(kSqrt2Pi), nd.bmax); // ds/db at s_c
-      const R sl = sc - R(kSqrtPiOver2) * (R(1) - e);
+      const R sl = node_sl<R>(ax, uf, sc, e);
       const R bc = R(0.5) * nd.bmax * (R(1) - e);
       const R bl = nd.bn;
       const bool blp = gt0(bl);
