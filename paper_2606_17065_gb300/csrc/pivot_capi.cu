@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
   // per row slot (carry slots first, then the tile's): its node, in structure-of-arrays form
   extern __shared__ double smem[];
   double* s_x = smem;
-  double* s_bmax = s_x + kSlots;
-  double* s_e = s_bmax + kSlots;
+  double* s_rsq = s_x + kSlots;   // 1/sqrt(F K); b_max = min(F, K) rsq is formed from it
+  double* s_e = s_rsq + kSlots;
   double* s_bn = s_e + kSlots;
   double* s_bsn = s_bn + kSlots;
   double* s_bb = s_bsn + kSlots;
@@ -305,10 +305,10 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         const int64_t i = base + (r - kCarry);
         const double K = a.K[i];
         const double F = kBS ? a.F[i] * s_ec[r] : a.F[i];
-        double x, bmax;
-        pivot::moneyness(F, K, x, bmax);
-        const double rsq = rsqrt(F * K);
+        double x, bmax, rsq;
+        pivot::moneyness(F, K, x, bmax, rsq);
         const double beta = s_bb[r] * rsq, betac = s_e[r] * rsq;
+        s_rsq[r] = rsq;
         bool fp64_row = true;
         // range tests on bit patterns (beta, beta_c and -x are non-negative): integer instructions
         const bool beta_f = pivot::gt_pos(beta, kMixedFloor), betac_f = pivot::gt_pos(betac, kMixedFloor);
@@ -320,7 +320,6 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
           fp64_row = false;
           rg = kDeepBin;
           s_x[r] = x;
-          s_bmax[r] = bmax;
           s_bb[r] = beta;
         } else if (kMixed && beta_f && betac_f && x_f) {
           // float node and region; the float copies are exact in double storage
@@ -331,7 +330,6 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
             // x, b_max and beta (or beta_c) in double for the final FP64 step and the
             // adjoint; the float node packed two floats to a slot (no conversions)
             s_x[r] = x;
-            s_bmax[r] = bmax;
             s_bb[r] = (rg == pivot::kUpper) ? betac : beta;
             *reinterpret_cast<float2*>(&s_e[r]) = make_float2(nf.e, nf.bn);
             *reinterpret_cast<float2*>(&s_bn[r]) = make_float2(nf.bsn, nf.x);
@@ -342,7 +340,6 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
           pivot::Node<double> nd;
           rg = pivot::classify<double>(x, bmax, beta, betac, nd) + (kMixed ? 4 : 0);
           s_x[r] = nd.x;
-          s_bmax[r] = nd.bmax;
           s_e[r] = nd.e;
           s_bn[r] = nd.bn;
           s_bsn[r] = nd.bsn;
@@ -419,13 +416,15 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
                             : (bin < 4 ? bin : bin >= 6 ? int(pivot::kLower) : bin - 3);
       const bool float_row = kMixed && (bin < 4 || bin >= kDeepBin);
       const double bb = s_bb[r];
+      const double rsq = s_rsq[r];
+      const double bmax = pivot::bmax_of(F, K, rsq);
       double s = 0.0;
       pivot::Last last;
       // FP64 bins, and float-seeded rows whose float solve was not accepted, meet at one FP64 solve
       bool fp64 = !float_row;
       if (float_row) {
         if (deep) {
-          s = pivot::solve_deep_mixed64(s_x[r], s_bmax[r], bb, last);
+          s = pivot::solve_deep_mixed64(s_x[r], bmax, bb, last);
         } else {
           pivot::Node<float> nf;
           const float2 p0 = *reinterpret_cast<const float2*>(&s_e[r]);
@@ -437,7 +436,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
           nf.x = p1.y;
           nf.bmax = p2.x;
           nf.bb = p2.y;
-          s = pivot::solve_mixed64(rg, nf, s_x[r], s_bmax[r], bb, a.steps, last);
+          s = pivot::solve_mixed64(rg, nf, s_x[r], bmax, bb, a.steps, last);
         }
         fp64 = !pivot::pos_finite(s);
         if (counting && fp64) atomicAdd(&s_count[kCountReject], 1ull);
@@ -448,13 +447,12 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         if (float_row) {
           // not accepted: the FP64 node from the row's inputs (its shared slots hold the float node)
           const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
-          double x, bmax;
-          pivot::moneyness(F, K, x, bmax);
-          const double rsq = rsqrt(F * K);
-          rg64 = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
+          double x, bmax_w, rsq_w;
+          pivot::moneyness(F, K, x, bmax_w, rsq_w);
+          rg64 = pivot::classify<double>(x, bmax_w, q.tv * rsq_w, q.cv * rsq_w, nd);
         } else {
           nd.x = s_x[r];
-          nd.bmax = s_bmax[r];
+          nd.bmax = bmax;
           nd.e = s_e[r];
           nd.bn = s_bn[r];
           nd.bsn = s_bsn[r];
@@ -474,8 +472,8 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         const double g = a.gbar ? a.gbar[i] : 1.0;
         const double gate_tau = kBS ? a.tau * s_er[r] : a.tau;  // G_tau on the cash vega e^{-r tau} V
         const pivot::Grad d = pivot::nan64(g) ? pivot::degenerate_grad(true, g, a.mode)
-                                       : pivot::adjoint_reuse(F, K, fl, sig, s, s_x[r], s_bmax[r], inv_sqT,
-                                                              rsqrt(F * K), g, gate_tau, a.mode, last);
+                                       : pivot::adjoint_reuse(F, K, fl, sig, s, s_x[r], bmax, inv_sqT, rsq, g,
+                                                              gate_tau, a.mode, last);
         if (kBS) {
           const pivot::BSGrad o = pivot::bs_grad(d, F, K, T, a.r[i], a.q[i], s_er[r], s_ec[r]);
           if (a.dP) a.dP[i] = o.dV;
@@ -499,7 +497,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
     for (int m = tid; m < nmv; m += kThreads) {
       const int src = s_mv_src[m], dst = s_mv_dst[m];
       s_x[dst] = s_x[src];
-      s_bmax[dst] = s_bmax[src];
+      s_rsq[dst] = s_rsq[src];
       s_e[dst] = s_e[src];
       s_bn[dst] = s_bn[src];
       s_bsn[dst] = s_bsn[src];

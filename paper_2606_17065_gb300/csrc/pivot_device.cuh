@@ -419,12 +419,41 @@ __device__ __forceinline__ double neg_abs_log_ratio(double mn, double mx, double
   return log_fp64(r) + c;
 }
 
-// x = -|ln(F/K)|, b_max = e^{x/2} = sqrt(min/max)
-__device__ __forceinline__ void moneyness(double F, double K, double& x, double& bmax) {
-  double r;
+// The wide-range form of moneyness (F K outside the normal range, or min/max below it,
+// i.e. |ln(F/K)| above ~708): rsq from the two factors, ln(min/max) from the IEEE quotient
+// and its residual while the quotient is normal, else as the difference of two logarithms
+// (no cancellation at that size).
+static __device__ __noinline__ void moneyness_wide(double mn, double mx, double& x, double& bmax, double& rsq) {
+  rsq = rsqrt(mn) * rsqrt(mx);
+  bmax = mn * rsq;
+  const double r = mn / mx;
+  if (r >= 0x1p-1022) x = -fabs(::log(r) + fma(-r, mx, mn) / mn);
+  else x = ::log(mn) - ::log(mx);
+}
+
+// b_max = min(F, K) / sqrt(F K) from rsq = 1/sqrt(F K): the one definition both
+// phases use, so that a row's b_max is the same wherever it is formed
+__device__ __forceinline__ double bmax_of(double F, double K, double rsq) { return (gt_pos(F, K) ? K : F) * rsq; }
+
+// x = -|ln(F/K)|, b_max = e^{x/2} = sqrt(min/max) and rsq = 1/sqrt(F K) from one
+// reciprocal square root: b_max = min(F, K) rsq, so r = b_max^2 is min/max to a few
+// ulps, and its residual c = (min - r max)/min (one fma, then times 1/min = rsq^2 max)
+// gives ln(min/max) = ln r + c to first order (|c| ~ 2^-50, its square far below
+// rounding): no division and no square root.  The sign is forced: x is never above 0.
+__device__ __forceinline__ void moneyness(double F, double K, double& x, double& bmax, double& rsq) {
   const bool fk = gt_pos(F, K); // F, K positive: integer order of the bit patterns
-  x = neg_abs_log_ratio(fk ? K : F, fk ? F : K, &r);
-  bmax = sqrt(r);
+  const double mn = fk ? K : F, mx = fk ? F : K;
+  const double p = F * K;
+  rsq = rsqrt(p);
+  bmax = mn * rsq;
+  const double r = bmax * bmax;
+  const uint64_t pb = uint64_t(__double_as_longlong(p)), rb = uint64_t(__double_as_longlong(r));
+  if (pb - 0x0010000000000000ull < 0x7fe0000000000000ull && rb >= 0x0010000000000000ull) {
+    const double c = fma(-r, mx, mn) * (rsq * rsq * mx);
+    x = -fabs(log_fp64(r) + c);
+  } else {
+    moneyness_wide(mn, mx, x, bmax, rsq);
+  }
 }
 
 // Stage 1 for one quote: validity, the time value tv = P - intrinsic (exact
@@ -479,7 +508,9 @@ __device__ __forceinline__ double log_beta(double beta, double F, double K, doub
 // interpolation nodes and the region tests, so float precision is far below
 // the guess's own interpolation error; SL keeps s_l's relative accuracy where
 // s_c - sqrt(pi/2)(1 - e) would cancel (u -> 0).  u >= 4096 (|F/K| beyond
-// e^4096) takes the evaluated node.
+// e^4096) takes the evaluated node, and so does the float node of the mixed
+// form, whose evaluation runs on the FP32 pipe and costs less than the table's
+// loads and conversions.
 // ---------------------------------------------------------------------------
 #include "node_table.inc"
 
@@ -581,7 +612,7 @@ __device__ __forceinline__ int classify(R x, R bmax, R beta, R betac, Node<R>& n
   using M = Math<R>;
   const R ax = -x;
   const float uf = to_float<R>(ax);
-  if (uf < kNodeMaxU) {
+  if (sizeof(R) == 8 && uf < kNodeMaxU) {
     // the tabulated node: b_c, and b_l, b_s(s_l) or b_max - b_u, b_s(s_u), all times b_max
     const NodeTab tb = node_tab(uf);
     const R e = from_float<R>(tb.e);
@@ -649,11 +680,11 @@ __device__ __forceinline__ double neg_ncdfinv<double>(double G, bool fast) {
 // while |x| < 4096, where s_l = |x| SL keeps its relative accuracy as |x| -> 0
 template <typename R>
 __device__ __forceinline__ R node_sc(R ax, float uf) {
-  return uf < kNodeMaxU ? R(kSqrt2) * from_float<R>(sqrtf(uf)) : Math<R>::sqrt_node_(R(2) * ax);
+  return (sizeof(R) == 8 && uf < kNodeMaxU) ? R(kSqrt2) * from_float<R>(sqrtf(uf)) : Math<R>::sqrt_node_(R(2) * ax);
 }
 template <typename R>
 __device__ __forceinline__ R node_sl(R ax, float uf, R sc, R e) {
-  if (uf < kNodeMaxU) {
+  if (sizeof(R) == 8 && uf < kNodeMaxU) {
     float w;
     return ax * from_float<R>(node_sl_u(uf, w));
   }
@@ -1275,8 +1306,8 @@ __device__ __forceinline__ void black_price_row(double F, double K, double T, do
   }
   const bool call = flag > 0;
   const double intrinsic = call ? fmax(F - K, 0.0) : fmax(K - F, 0.0);
-  double x, bmax;
-  moneyness(F, K, x, bmax);
+  double x, bmax, rsq;
+  moneyness(F, K, x, bmax, rsq);
   const double sqT = sqrt(T);
   const double rfk = sqrt(F * K);
   if (sigma == 0.0) {

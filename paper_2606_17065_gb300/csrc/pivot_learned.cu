@@ -32,8 +32,8 @@ struct LearnedRow {
 __device__ __forceinline__ LearnedRow learned_row(double F, double K, double T, double P, int fl) {
   LearnedRow r;
   const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
-  pivot::moneyness(F, K, r.x, r.bmax);
-  const double rsq = rsqrt(F * K);
+  double rsq;
+  pivot::moneyness(F, K, r.x, r.bmax, rsq);
   r.beta = q.tv * rsq;
   r.betac = q.cv * rsq;
   r.lnb = pivot::log_beta(r.beta, F, K, T, P, fl);
@@ -72,7 +72,7 @@ constexpr uint8_t kNoBin = 255;
 
 struct InferSmem {
   M::Weights W;
-  double x[kITile], bmax[kITile], bb[kITile];
+  double x[kITile], rsq[kITile], bb[kITile];  // rsq = 1/sqrt(F K); b_max = min(F, K) rsq
   float s0[kITile];
   uint16_t list[kITile], order[kITile], pos[kITile], fb[kITile];
   uint8_t bin[kITile];
@@ -87,7 +87,7 @@ constexpr int kIBins = 6;
 
 template <bool kBackward>
 __device__ __forceinline__ void finish_row(const Args& a, int64_t i, double F, double K, double T, int fl, double s,
-                                           double x, double bmax, const pivot::Last& last) {
+                                           double x, double bmax, double rsq, const pivot::Last& last) {
   const double inv_sqT = rsqrt(T);
   const double sig = s * inv_sqT;
   a.sigma[i] = sig;
@@ -95,7 +95,7 @@ __device__ __forceinline__ void finish_row(const Args& a, int64_t i, double F, d
   if (kBackward) {
     const double g = a.gbar ? a.gbar[i] : 1.0;
     const pivot::Grad d = isnan(g) ? pivot::degenerate_grad(true, g, a.mode)
-                                   : pivot::adjoint_reuse(F, K, fl, sig, s, x, bmax, inv_sqT, rsqrt(F * K), g,
+                                   : pivot::adjoint_reuse(F, K, fl, sig, s, x, bmax, inv_sqT, rsq, g,
                                                           a.tau, a.mode, last);
     if (a.dP) a.dP[i] = d.dP;
     if (a.dF) a.dF[i] = d.dF;
@@ -169,12 +169,11 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       const int r = has ? S.list[qi] : 0;
       bool learned = false;
       float f0 = 0.0f, f1 = 0.5f, bf = 0.0f;
-      double x = 0.0, bmax = 0.0, beta = 0.0, betac = 0.0;
+      double x = 0.0, bmax = 0.0, rsq = 0.0, beta = 0.0, betac = 0.0;
       if (has) {
         const int64_t i = base + r;
         const double F = a.F[i], K = a.K[i];
-        pivot::moneyness(F, K, x, bmax);
-        const double rsq = rsqrt(F * K);
+        pivot::moneyness(F, K, x, bmax, rsq);
         beta = S.bb[r] * rsq;
         betac = S.x[r] * rsq;
         learned = beta > 1e-30 && betac > 1e-30 && x > -80.0;
@@ -188,7 +187,7 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       int bin = -1;
       if (has) {
         S.x[r] = x;
-        S.bmax[r] = bmax;
+        S.rsq[r] = rsq;
         if (!learned && !(beta > 1e-30) && betac > 1e-30 && x <= -0.1 && x > -80.0 && pivot::pos_normal(beta)) {
           bin = 3;
           S.bb[r] = beta;
@@ -234,11 +233,12 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       if (b == 3) {
         // deep lower tail
         pivot::Last last;
-        const double x = S.x[r], bmax = S.bmax[r];
+        const int64_t i = base + r;
+        const double F = a.F[i], K = a.K[i];
+        const double x = S.x[r], rsq = S.rsq[r], bmax = pivot::bmax_of(F, K, rsq);
         const double s = pivot::solve_deep_mixed64(x, bmax, S.bb[r], last);
         if (pivot::pos_finite(s)) {
-          const int64_t i = base + r;
-          finish_row<kBackward>(a, i, a.F[i], a.K[i], a.T[i], a.flag[i], s, x, bmax, last);
+          finish_row<kBackward>(a, i, F, K, a.T[i], a.flag[i], s, x, bmax, rsq, last);
         } else {
           S.fb[atomicAdd(&S.nfb, 1)] = uint16_t(r);
         }
@@ -246,7 +246,9 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       }
       const int bn = b >= 4 ? b - 4 : b;
       const int rg = bn == 0 ? pivot::kLower : bn == 1 ? pivot::kMidHigh : pivot::kUpper;
-      const double x = S.x[r], bb = S.bb[r], bmax = S.bmax[r];
+      const int64_t i = base + r;
+      const double F = a.F[i], K = a.K[i];
+      const double x = S.x[r], bb = S.bb[r], rsq = S.rsq[r], bmax = pivot::bmax_of(F, K, rsq);
       const float xf = float(x), bbf = float(bb);
       const float lnb = (rg == pivot::kMidHigh) ? 0.0f : logf(bbf);
       const float lnbetac = (rg == pivot::kUpper) ? lnb : 0.0f;
@@ -262,8 +264,7 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
         ok = fabs(s - double(sf)) <= kAcceptFinal * s;
       }
       if (ok) {
-        const int64_t i = base + r;
-        finish_row<kBackward>(a, i, a.F[i], a.K[i], a.T[i], a.flag[i], s, x, bmax, last);
+        finish_row<kBackward>(a, i, F, K, a.T[i], a.flag[i], s, x, bmax, rsq, last);
       } else {
         S.fb[atomicAdd(&S.nfb, 1)] = uint16_t(r);
       }
@@ -277,15 +278,14 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
       const int fl = a.flag[i];
       const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
-      double x, bmax;
-      pivot::moneyness(F, K, x, bmax);
-      const double rsq = rsqrt(F * K);
+      double x, bmax, rsq;
+      pivot::moneyness(F, K, x, bmax, rsq);
       pivot::Node<double> nd;
       const int rg = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
       const double lnb = (rg == pivot::kLower) ? pivot::log_beta(nd.bb, F, K, T, P, fl) : 0.0;
       pivot::Last last;
       const double s = pivot::solve64(rg, nd, lnb, a.steps, last);
-      finish_row<kBackward>(a, i, F, K, T, fl, s, x, bmax, last);
+      finish_row<kBackward>(a, i, F, K, T, fl, s, x, bmax, rsq, last);
     }
     __syncthreads();
     if (counting && tid == 0) {
@@ -312,9 +312,8 @@ __global__ void __launch_bounds__(kBlock) k_guess_rational(int64_t n, const doub
     const pivot::Quote q = pivot::classify_quote(F[i], K[i], T[i], P[i], flag[i]);
     double s = __longlong_as_double(0x7ff8000000000000LL);
     if (q.status == 0) {
-      double x, bmax;
-      pivot::moneyness(F[i], K[i], x, bmax);
-      const double rsq = rsqrt(F[i] * K[i]);
+      double x, bmax, rsq;
+      pivot::moneyness(F[i], K[i], x, bmax, rsq);
       pivot::Node<double> nd;
       const int rg = pivot::classify<double>(x, bmax, q.tv * rsq, q.cv * rsq, nd);
       const double lnb = (rg == pivot::kLower) ? pivot::log_beta(nd.bb, F[i], K[i], T[i], P[i], flag[i]) : 0.0;
