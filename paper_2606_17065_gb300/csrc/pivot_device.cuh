@@ -391,21 +391,14 @@ __device__ __forceinline__ bool bad_inputs(double F, double K, double T, int fla
   return !pos_finite(F) || !pos_finite(K) || !pos_finite(T) || (flag != 1 && flag != -1);
 }
 
-// P - F + K (call) or P - K + F (put), in the money: P - a + b with a > b > 0, rounded once.
-// By Sterbenz's lemma a - b is exact when a <= 2b, and P - a is exact when a/2 <= P <= 2a, so
-// one of P - (a - b) and (P - a) + b takes a single rounding on every price in or near the
-// no-arbitrage interval [a - b, a]; two error-free TwoSums cover the rest (a > 2b and P below
-// a/2, a price far under the intrinsic value).  Positive doubles compare as their bit patterns.
-__device__ __forceinline__ double time_value_itm(double P, double a, double b) {
-  const double two_b = b + b, half_a = 0.5 * a;
-  if (__double_as_longlong(a) <= __double_as_longlong(two_b)) return P - (a - b);
-  if (__double_as_longlong(P) >= __double_as_longlong(half_a)) return (P - a) + b;
-  double s1 = P - a, bb = s1 - P;
-  double e1 = (P - (s1 - bb)) + (-a - bb);
-  double s2 = s1 + b;
-  double bb2 = s2 - s1;
-  double e2 = (s1 - (s2 - bb2)) + (b - bb2);
-  return s2 + (e1 + e2);
+// 2v for a non-negative finite double v from its bit pattern, on the integer pipes: a
+// subnormal doubles its integer (crossing into the normal range correctly), a normal one
+// gains one in its exponent, and beyond the range the result is +inf.  A negative v gives
+// a negative pattern, which every *_pos test orders below all non-negative values.
+__device__ __forceinline__ double twice_pos(double v) {
+  const int64_t b = __double_as_longlong(v);
+  const int64_t e = b >> 52;
+  return __longlong_as_double(e == 0 ? (b << 1) : (e >= 2046 ? 0x7ff0000000000000LL : b + (1LL << 52)));
 }
 
 // -|ln(F/K)| from mn = min(F, K), mx = max(F, K), branch-free and accurate
@@ -477,10 +470,20 @@ __device__ __forceinline__ Quote classify_quote(double F, double K, double T, do
     q.sigma = qnan;
     return q;
   }
+  // U = a (F for calls, K for puts), intrinsic a - b in the money (a > b).  The time value
+  // P - a + b is rounded once: by Sterbenz's lemma b - a is exact when a <= 2b, and P - a is
+  // exact when a/2 <= P <= 2a, so P + (b - a) or (P - a) + b covers every price in or near the
+  // no-arbitrage interval [a - b, a].  Below it, with a > 2b and P < a/2, P < a/2 < a - b: the
+  // time value is negative whatever its rounding, and only its sign is used.  The same three
+  // FP64 additions serve every lane (no branch), and U - P = -(P - a) exactly.
   const bool call = flag > 0;
-  const bool itm = call ? gt_pos(F, K) : gt_pos(K, F);
-  q.tv = itm ? (call ? time_value_itm(P, F, K) : time_value_itm(P, K, F)) : P;
-  q.cv = (call ? F : K) - P;
+  const double a = call ? F : K, b = call ? K : F;
+  const bool itm = gt_pos(a, b);
+  const double d = P - a;
+  const bool near = le_pos(a, twice_pos(b));
+  const double tv = (near ? P : d) + (near ? b - a : b);
+  q.tv = !itm ? P : (!near && gt_pos(a, twice_pos(P))) ? -1.0 : tv;
+  q.cv = -d;
   if (neg64(q.tv)) { q.status = 1; q.sigma = qnan; }
   else if (neg64(q.cv)) { q.status = 2; q.sigma = qnan; }
   else if (zero64(q.tv)) { q.status = 4; q.sigma = 0.0; }
@@ -1187,7 +1190,8 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   } else {
     ibs = exp_fp64(-lbs);
   }
-  double E1 = bmax * ibs, E2 = div_fast(ibs, bmax);
+  // 1/b_max = max(F, K) rsq
+  double E1 = bmax * ibs, E2 = ibs * ((gt_pos(F, K) ? F : K) * rsq);
   if (!finite64(ibs)) {
     // b_s underflows (|ln(F/K)| beyond ~1400): the reflections from their own exponents
     E1 = kSqrt2Pi * exp_fp64(0.5 * hpt * hpt);
