@@ -114,13 +114,17 @@ __global__ void __launch_bounds__(kBlock) k_bs_iv_backward(Args a) {
 
 // ---------------------------------------------------------------------------
 // Forward (and fused forward+backward) with per-tile compaction and region
-// binning.  A block owns a tile of consecutive rows (kTile, or fewer on a batch
-// too small to give every resident block a full tile).
-//  phase 1: every thread classifies tile/kThreads rows (coalesced loads) with
-//           the cheap stage-1 tests; rows that need no solve (invalid, or at
-//           a bound of the price interval) are finished at once, the others
-//           are appended to a tile-local list (one warp-aggregated atomic).
-//  phase 2: the list is consumed densely: normalisation, LBR boundary node
+// binning.  The input is cut into chunks of kThreads consecutive rows, dealt to
+// the persistent blocks in grid-stride order.  A block's tile is a set of solve
+// slots (kCap), filled from as many chunks as they can take:
+//  phase 1: passes of up to kCap/kThreads chunks, one row per thread and chunk
+//           (coalesced loads), with the cheap stage-1 tests; rows that need no
+//           solve (invalid, or at a bound of the price interval) are finished
+//           at once, the others take the next free slot (one warp-aggregated
+//           atomic) with their time value and its complement.  Passes go on
+//           while the free slots can hold one more chunk whatever it holds,
+//           so a batch where most rows end in stage 1 still fills the tile.
+//  phase 2: the slots are consumed densely: normalisation, LBR boundary node
 //           and region of each row, kept in shared memory, counted per region.
 //  phase 3: the rows are laid out region after region and consumed in that
 //           order, so a warp runs one region's guess and Householder
@@ -130,7 +134,6 @@ __global__ void __launch_bounds__(kBlock) k_bs_iv_backward(Args a) {
 //           that no warp runs with idle lanes or two regions' code, except in
 //           the block's last tile, which takes every row.  sigma and the gated
 //           adjoint are written here.
-// The grid is persistent: blocks stride over tiles.
 // ---------------------------------------------------------------------------
 // Region bins.  FP64 form: the 4 regions, plus bins 4, 5 for middle-region
 // rows and bin 7 for lower-region rows near the money (|x| <= kTaylorX), the
@@ -147,27 +150,30 @@ __global__ void __launch_bounds__(kBlock) k_bs_iv_backward(Args a) {
 constexpr int kMaxBins = 12;
 // Rows a bin may carry from one tile to the next (its last, partial warp).
 constexpr int kCarryPerBin = 31;
+// Chunks one tile may draw from (bounds the table of their first rows).
+constexpr int kMaxChunks = 32;
 
 // Shared memory of the binned kernel, in row slots: kCarry slots hold the
 // rows carried over from earlier tiles (bin b in [31 b, 31 b + 31)), then
-// kTile slots the current tile's rows.  Per slot: six node fields (+ e^{r tau},
-// e^{(r-q) tau} in the Black-Scholes form) and the phase-3 order (whose first
-// kTile entries also serve as the phase 1 -> 2 list); per carry slot: the
-// row's global index and a move record.  Tiles: 1,792 rows for the FP64
-// Black-76 form, 1,536 for its mixed form (12 bins), 1,280 / 1,024 for the
-// Black-Scholes forms, so that 2 blocks of 256 threads fit an SM (~128
-// registers a thread).
+// kCap slots the current tile's solved rows.  Per slot: six node fields
+// (+ e^{r tau}, e^{(r-q) tau} in the Black-Scholes form) and the phase-3
+// order; per tile slot: the row's chunk and lane (a 16-bit code); per carry
+// slot: the row's global index and a move record.  Slots per tile: 1,792 for
+// the FP64 Black-76 form, 1,536 for its mixed form (12 bins), 1,280 / 1,024
+// for the Black-Scholes forms, so that 2 blocks of 256 threads fit an SM
+// (~128 registers a thread).
 template <bool kBS, bool kMixed>
 struct TileCfg {
   static constexpr int kBins = kMixed ? 12 : 8;
   static constexpr int kCarry = kCarryPerBin * kBins;
-  static constexpr int kThreads = 256;
+  static constexpr int kThreads = 256;  // also the rows of a chunk
   static constexpr int kMinBlocks = 2;
-  static constexpr int kTile = kBS ? (kMixed ? 1024 : 1280) : (kMixed ? 1536 : 1792);
-  static constexpr int kRowsPerThread = kTile / kThreads;
-  static constexpr int kSlots = kCarry + kTile;
+  static constexpr int kCap = kBS ? (kMixed ? 1024 : 1280) : (kMixed ? 1536 : 1792);
+  static constexpr int kMaxPass = kCap / kThreads;  // chunks per phase-1 pass, rows per thread in phase 2
+  static constexpr int kSlots = kCarry + kCap;
   static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kSlots * sizeof(double) + size_t(kCarry) * sizeof(int64_t) +
-                                  size_t(kSlots) * sizeof(uint16_t) + 2 * size_t(kCarry) * sizeof(uint16_t);
+                                  size_t(kSlots) * sizeof(uint16_t) + size_t(kCap) * sizeof(uint16_t) +
+                                  2 * size_t(kCarry) * sizeof(uint16_t);
 };
 constexpr int kDeepBin = 8;
 constexpr double kMixedFloor = 1e-30;
@@ -194,8 +200,9 @@ template <bool kBackward, bool kMixed, bool kBS>
 __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, kMixed>::kMinBlocks)
     k_iv_binned(Args a) {
   using Cfg = TileCfg<kBS, kMixed>;
-  constexpr int kRowsPerThread = Cfg::kRowsPerThread;
   constexpr int kThreads = Cfg::kThreads;
+  constexpr int kMaxPass = Cfg::kMaxPass;
+  constexpr int kCap = Cfg::kCap;
   constexpr int kBins = Cfg::kBins;
   constexpr int kCarry = Cfg::kCarry;
   constexpr int kSlots = Cfg::kSlots;
@@ -211,9 +218,10 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
   double* s_ec = s_er + (kBS ? kSlots : 0);          // kBS only
   int64_t* s_gidx = reinterpret_cast<int64_t*>(s_ec + (kBS ? kSlots : 0));  // global row of a carry slot
   uint16_t* s_order = reinterpret_cast<uint16_t*>(s_gidx + kCarry);         // phase 2 -> 3: slots in bin order
-  uint16_t* s_list = s_order;   // phase 1 -> 2: slots to solve (read into registers before the order is written)
-  uint16_t* s_mv_src = s_order + kSlots;                                     // leftover rows: tile slot ...
-  uint16_t* s_mv_dst = s_mv_src + kCarry;                                    // ... -> carry slot
+  uint16_t* s_code = s_order + kSlots;    // tile slot -> (chunk of the tile << 8) | row in the chunk
+  uint16_t* s_mv_src = s_code + kCap;     // leftover rows: tile slot ...
+  uint16_t* s_mv_dst = s_mv_src + kCarry; // ... -> carry slot
+  __shared__ int64_t s_cbase[kMaxChunks];  // first row of each chunk of the tile
   __shared__ int s_nsolve, s_nmv;
   __shared__ int s_cnt[kMaxBins];   // rows per bin, carried ones included
   __shared__ int s_full[kMaxBins];  // rows per bin consumed by this tile
@@ -225,84 +233,106 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
   const int lane = tid & 31;
   const bool counting = a.counters != nullptr;
   if (counting && tid < PIVOT_COUNTERS_LEN) s_count[tid] = 0;
-  // rows per tile for this launch: the launcher shrinks tiles on small batches so that
-  // every SM gets work; the shared arrays keep their kTile strides
-  const int tile = a.tile;
-  const int jmax = tile / kThreads;
+  // global row of a slot
+  auto row_of = [&](int r) -> int64_t {
+    if (r < kCarry) return s_gidx[r];
+    const int c = s_code[r - kCarry];
+    return s_cbase[c >> 8] + (c & 0xff);
+  };
+  const int64_t nchunks = (a.n + kThreads - 1) / kThreads;
+  int64_t cursor = blockIdx.x;  // this block's next chunk
   if (tid < kBins) s_ccnt[tid] = 0;
-  for (int64_t base = int64_t(blockIdx.x) * tile; base < a.n; base += int64_t(gridDim.x) * tile) {
-    const bool last = base + int64_t(gridDim.x) * tile >= a.n;  // the block's last tile takes every row
+  while (cursor < nchunks) {
     if (tid < kBins) s_cnt[tid] = s_ccnt[tid];  // carried rows come first in their bins
     if (tid == 0) {
       s_nsolve = 0;
       s_nmv = 0;
     }
     __syncthreads();
-    // ---- phase 1
+    // ---- phase 1: passes over this block's next chunks while the free slots can take them
+    int nsolve = 0, nch = 0;
+    while (cursor < nchunks) {
+      int take = (kCap - nsolve) / kThreads;
+      if (take > kMaxChunks - nch) take = kMaxChunks - nch;
+      if (take <= 0) break;
 #pragma unroll
-    for (int j = 0; j < kRowsPerThread; ++j) {
-      const int r = kCarry + j * kThreads + tid;  // slot
-      const int64_t i = base + (j * kThreads + tid);
-      bool solve = false;
-      int row_status = -1;
-      if (j < jmax && i < a.n) {
-        const double K = a.K[i], T = a.T[i];
-        double rr = 0.0, qq = 0.0;
-        if (kBS) {
-          rr = a.r[i];
-          qq = a.q[i];
-          pivot::bs_factors(T, rr, qq, s_er[r], s_ec[r]);
-        }
-        double F, P;
-        row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
-        const int fl = a.flag[i];
-        const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
-        row_status = q.status;
-        if (q.status != 0) {
-          a.sigma[i] = q.sigma;
-          if (a.status) a.status[i] = uint8_t(q.status);
-          if (kBackward) {
-            // outside the open price interval, or invalid: the degenerate gradient of its status
-            const double g = a.gbar ? a.gbar[i] : 1.0;
-            const double v = pivot::degenerate_grad(q.status <= 3 || pivot::nan64(g), g, a.mode).dP;
-            if (a.dP) a.dP[i] = v;
-            if (a.dF) a.dF[i] = v;
-            if (a.dK) a.dK[i] = v;
-            if (a.dT) a.dT[i] = v;
-            if (kBS) {
-              if (a.dr) a.dr[i] = v;
-              if (a.dq) a.dq[i] = v;
-            }
+      for (int j = 0; j < kMaxPass; ++j) {
+        if (j >= take) break;  // uniform over the block
+        const int64_t c = cursor + int64_t(j) * gridDim.x;
+        const int64_t i = c * kThreads + tid;
+        if (tid == 0 && c < nchunks) s_cbase[nch + j] = c * kThreads;
+        bool solve = false;
+        int row_status = -1;
+        double tv = 0.0, cv = 0.0, er = 1.0, ec = 1.0;
+        if (i < a.n) {
+          const double K = a.K[i], T = a.T[i];
+          double F = a.F[i], P = a.P[i];
+          if (kBS) {
+            pivot::bs_factors(T, a.r[i], a.q[i], er, ec);
+            F *= ec;
+            P *= er;
           }
-        } else {
-          solve = true;
-          // the time value and its complement, for phase 2 (their slots are free until then)
-          s_bb[r] = q.tv;
-          s_e[r] = q.cv;
+          const int fl = a.flag[i];
+          const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
+          row_status = q.status;
+          if (q.status != 0) {
+            a.sigma[i] = q.sigma;
+            if (a.status) a.status[i] = uint8_t(q.status);
+            if (kBackward) {
+              // outside the open price interval, or invalid: the degenerate gradient of its status
+              const double g = a.gbar ? a.gbar[i] : 1.0;
+              const double v = pivot::degenerate_grad(q.status <= 3 || pivot::nan64(g), g, a.mode).dP;
+              if (a.dP) a.dP[i] = v;
+              if (a.dF) a.dF[i] = v;
+              if (a.dK) a.dK[i] = v;
+              if (a.dT) a.dT[i] = v;
+              if (kBS) {
+                if (a.dr) a.dr[i] = v;
+                if (a.dq) a.dq[i] = v;
+              }
+            }
+          } else {
+            solve = true;
+            tv = q.tv;
+            cv = q.cv;
+          }
         }
-      }
-      const int slot = warp_append(solve, &s_nsolve, lane);
-      if (solve) s_list[slot] = uint16_t(r);
-      if (counting) {
+        const int r = kCarry + warp_append(solve, &s_nsolve, lane);
+        if (solve) {
+          // the time value and its complement, for phase 2
+          s_bb[r] = tv;
+          s_e[r] = cv;
+          s_code[r - kCarry] = uint16_t(((nch + j) << 8) | tid);
+          if (kBS) {
+            s_er[r] = er;
+            s_ec[r] = ec;
+          }
+        }
+        if (counting) {
 #pragma unroll
-        for (int k = 1; k < 6; ++k) {
-          const unsigned m = __ballot_sync(0xffffffffu, row_status == k);
-          if (lane == 0 && m) atomicAdd(&s_count[k], (unsigned long long)__popc(m));
+          for (int k = 1; k < 6; ++k) {
+            const unsigned m = __ballot_sync(0xffffffffu, row_status == k);
+            if (lane == 0 && m) atomicAdd(&s_count[k], (unsigned long long)__popc(m));
+          }
         }
       }
+      cursor += int64_t(take) * gridDim.x;
+      nch += take;
+      __syncthreads();
+      nsolve = s_nsolve;
+      __syncthreads();  // every thread has read the count before the next pass adds to it
     }
-    __syncthreads();
+    const bool last = cursor >= nchunks;  // the block's last tile takes every row
     // ---- phase 2
-    const int nsolve = s_nsolve;
-    int reg[kRowsPerThread], pos[kRowsPerThread], row[kRowsPerThread];
+    int reg[kMaxPass], pos[kMaxPass], row[kMaxPass];
 #pragma unroll
-    for (int j = 0; j < kRowsPerThread; ++j) {
+    for (int j = 0; j < kMaxPass; ++j) {
       const int qi = j * kThreads + tid;
       int rg = -1;
       row[j] = 0;
       if (qi < nsolve) {
-        const int r = s_list[qi];
-        const int64_t i = base + (r - kCarry);
+        const int r = kCarry + qi;
+        const int64_t i = row_of(r);
         const double K = a.K[i];
         const double F = kBS ? a.F[i] * s_ec[r] : a.F[i];
         double x, bmax, rsq;
@@ -379,7 +409,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kRowsPerThread; ++j) {
+    for (int j = 0; j < kMaxPass; ++j) {
       const int b = reg[j];
       if (b >= 0) {
         const int p = pos[j], full = s_full[b];
@@ -401,12 +431,13 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
     __syncthreads();
     // ---- phase 3
     const int total = s_off[kBins];
+    const int nmv = s_nmv;  // final since the barrier above; the next tile resets it
     for (int qi = tid; qi < total; qi += kThreads) {
       const int r = s_order[qi];  // slot
       int bin = 0;
 #pragma unroll
       for (int k = 1; k < kBins; ++k) bin += (qi >= s_off[k]) ? 1 : 0;
-      const int64_t i = r < kCarry ? s_gidx[r] : base + (r - kCarry);
+      const int64_t i = row_of(r);
       const double K = a.K[i], T = a.T[i];
       double F, P;
       row_fp<kBS>(a, i, r, s_er, s_ec, F, P);
@@ -493,7 +524,6 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
     __syncthreads();
     // the partial warps' rows to their carry slots, now that phase 3 has read the slots they
     // take; the next tile's first barrier orders these copies before its phase 1
-    const int nmv = s_nmv;
     for (int m = tid; m < nmv; m += kThreads) {
       const int src = s_mv_src[m], dst = s_mv_dst[m];
       s_x[dst] = s_x[src];
@@ -506,7 +536,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         s_er[dst] = s_er[src];
         s_ec[dst] = s_ec[src];
       }
-      s_gidx[dst] = base + (src - kCarry);
+      s_gidx[dst] = row_of(src);
     }
     if (tid < kBins) s_ccnt[tid] = s_cnt[tid] - s_full[tid];
   }
@@ -532,14 +562,13 @@ int check_opts(const pivot_opts* o, int* steps, int* mode) {
   return PIVOT_OK;
 }
 
-// persistent grid for the binned kernels: resident blocks x SMs, capped by the tiles
+// persistent grid for the binned kernels: resident blocks x SMs, capped by the chunks
 template <bool kBackward, bool kMixed, bool kBS = false>
 int launch_binned(const Args& a, void* stream) {
   // occupancy of this instantiation, looked up once per device
   static thread_local int configured_device = -1;
   static thread_local int blocks_per_sm = 0, num_sms = 0;
   constexpr size_t smem = TileCfg<kBS, kMixed>::kSmem;
-  constexpr int kTile = TileCfg<kBS, kMixed>::kTile;
   constexpr int kThreads = TileCfg<kBS, kMixed>::kThreads;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
@@ -553,15 +582,9 @@ int launch_binned(const Args& a, void* stream) {
     configured_device = dev;
   }
   const int64_t cap = int64_t(blocks_per_sm) * num_sms;
-  // the largest tile (a multiple of the block) that still gives every resident block a tile
-  int64_t tile = (a.n + cap - 1) / cap;
-  tile = ((tile + kThreads - 1) / kThreads) * kThreads;
-  if (tile > kTile) tile = kTile;
-  Args b = a;
-  b.tile = int(tile);
-  const int64_t tiles = (a.n + tile - 1) / tile;
-  const unsigned grid = unsigned(tiles < cap ? tiles : cap);
-  k_iv_binned<kBackward, kMixed, kBS><<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(b);
+  const int64_t chunks = (a.n + kThreads - 1) / kThreads;  // every block gets at least one
+  const unsigned grid = unsigned(chunks < cap ? chunks : cap);
+  k_iv_binned<kBackward, kMixed, kBS><<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(a);
   return launch_status();
 }
 

@@ -29,9 +29,6 @@ struct Args {
   // dP / dF / dT receive dsigma/dV, dsigma/dS, dsigma/dtau; r, q per row
   const double *r, *q;
   double *dr, *dq;
-  // rows per tile of the binned kernel (a multiple of its block size, at most
-  // its compile-time tile); 0 = the largest; set by the launcher
-  int tile;
   // PIVOT_COUNTERS_LEN per-launch counters (pivot_opts.counters), or NULL
   unsigned long long* counters;
 };
