@@ -44,22 +44,22 @@ BYTES_PER_ROW = 33 + 41
 # over one launch of 4,194,304 stress rows, divided by the rows), see
 # profiles/k_iv_binned_fwdbwd_stress.md.  Counts scale with the rows: every
 # launch of the same distribution does the same work per row on average.
-FLOPS_PER_ROW = 323.0
+FLOPS_PER_ROW = 260.2
 # dram__bytes_read.sum + dram__bytes_write.sum per row from the same capture.
-TRAFFIC_PER_ROW = 101.6
+TRAFFIC_PER_ROW = 132.7
 # Executed FLOPs per row of the other measured forms, counted by ncu the same way on one launch
 # of 4,194,304 rows of each workload (python bench.py --case <name> --rows 4194304; FP32 from
 # smsp__sass_thread_inst_executed_op_{fadd,fmul}_pred_on + 2 x ..._ffma_pred_on), see
 # profiles/flops_per_row_all_forms.md.
 FLOPS = {
     # case: (FP64 FLOP / row, FP32 FLOP / row)
-    "stress": (FLOPS_PER_ROW, 18.7),
-    "stress-mixed": (114.2, 231.7),
-    "body": (682.7, 27.3),
-    "body-mixed": (266.5, 508.9),
-    "body-learned": (265.8, 1589.0),
-    "bs-wide": (422.6, 22.6),
-    "bs-wide-mixed": (180.4, 271.7),
+    "stress": (FLOPS_PER_ROW, 51.4),
+    "stress-mixed": (96.8, 231.9),
+    "body": (534.7, 102.7),
+    "body-mixed": (224.9, 508.9),
+    "body-learned": (224.1, 1589.0),
+    "bs-wide": (350.9, 60.9),
+    "bs-wide-mixed": (160.3, 271.9),
 }
 # MLP inference of the learned seed, 2 -> 64 -> 64 -> 64 -> 1: 2 (2 64 + 64 64 + 64 64 + 64) FLOP
 # per seeded row on the BF16 tensor cores (algorithmic count)
@@ -500,6 +500,8 @@ def svi_variant(dev, n_surfaces=1024, steps=100):
     sum (sigma_hat - sigma*)^2, 100 steps at lr 1e-3, smooth gate tau = 1e-6."""
     from paper_2606_17065_gb300 import training
     batch = workloads.svi_batch(n_surfaces, seed=5)
+    # untimed warm-up: the first steps load torch's CUDA kernels (seconds on a fresh machine)
+    training.train_iv_loss(batch, steps=3, lr=1e-3, tau=1e-6, gate="smooth", device=dev)
     out = training.train_iv_loss(batch, steps=steps, lr=1e-3, tau=1e-6, gate="smooth", device=dev)
     L = out["loss"]
     return {"workload": f"svi-{n_surfaces}: ragged 50-400 quotes over 8 maturities, MLP 2->128x4->1 per surface, "

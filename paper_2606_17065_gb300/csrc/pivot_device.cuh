@@ -1150,12 +1150,13 @@ __device__ __forceinline__ Grad adjoint_core(double F, double K, int flag, doubl
   return out;
 }
 
-// Y(z0 + d) to second order from Y(z0): Y' = 1 + zY, Y'' = z + (1 + z^2) Y.
-// |d| <~ 1e-5 |z0| at the final iterate of every solve, so the third-order
-// term (Y''' d^3 / 6, relative ~ d^3 / |z|^3 for z < 0) is below 1e-15.
+// Y(z0 + d) to second order from Y(z0): Y' = 1 + zY, Y'' = z + (1 + z^2) Y
+// = z Y' + Y.  |d| <~ 1e-5 |z0| at the final iterate of every solve, so the
+// third-order term (Y''' d^3 / 6, relative ~ d^3 / |z|^3 for z < 0) is below
+// 1e-15.
 __device__ __forceinline__ double mills_shift(double y0, double z0, double d) {
   const double y1 = fma(z0, y0, 1.0);
-  const double y2 = fma(fma(z0, z0, 1.0), y0, z0);
+  const double y2 = fma(z0, y1, y0);
   return fma(fma(0.5 * y2, d, y1), d, y0);
 }
 
