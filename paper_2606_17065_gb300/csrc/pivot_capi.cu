@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         if (tid == 0 && c < nchunks) s_cbase[nch + j] = c * kThreads;
         bool solve = false;
         int row_status = -1;
-        double tv = 0.0, cv = 0.0, er = 1.0, ec = 1.0;
+        double tv = 0.0, cv = 0.0, er = 1.0, ec = 1.0, Fs = 0.0, Ks = 0.0;
         if (i < a.n) {
           const double K = a.K[i], T = a.T[i];
           double F = a.F[i], P = a.P[i];
@@ -275,9 +275,10 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
           const int fl = a.flag[i];
           const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
           row_status = q.status;
+          // every row's status here, in row order (a solved row's stays 0): one coalesced byte
+          if (a.status) a.status[i] = uint8_t(q.status);
           if (q.status != 0) {
             a.sigma[i] = q.sigma;
-            if (a.status) a.status[i] = uint8_t(q.status);
             if (kBackward) {
               // outside the open price interval, or invalid: the degenerate gradient of its status
               const double g = a.gbar ? a.gbar[i] : 1.0;
@@ -295,13 +296,17 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
             solve = true;
             tv = q.tv;
             cv = q.cv;
+            Fs = F;
+            Ks = K;
           }
         }
         const int r = kCarry + warp_append(solve, &s_nsolve, lane);
         if (solve) {
-          // the time value and its complement, for phase 2
+          // the time value and its complement, and F and K in the slots phase 2 fills from them
           s_bb[r] = tv;
           s_e[r] = cv;
+          s_x[r] = Fs;
+          s_rsq[r] = Ks;
           s_code[r - kCarry] = uint16_t(((nch + j) << 8) | tid);
           if (kBS) {
             s_er[r] = er;
@@ -332,9 +337,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
       row[j] = 0;
       if (qi < nsolve) {
         const int r = kCarry + qi;
-        const int64_t i = row_of(r);
-        const double K = a.K[i];
-        const double F = kBS ? a.F[i] * s_ec[r] : a.F[i];
+        const double F = s_x[r], K = s_rsq[r];  // left by phase 1 (forward F in the Black-Scholes form)
         double x, bmax, rsq;
         pivot::moneyness(F, K, x, bmax, rsq);
         const double beta = s_bb[r] * rsq, betac = s_e[r] * rsq;
@@ -497,7 +500,6 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
       const double inv_sqT = rsqrt(T);
       const double sig = s * inv_sqT;
       a.sigma[i] = sig;
-      if (a.status) a.status[i] = 0;
       if (kBackward) {
         // the adjoint at the solved s, reusing x and 1/sqrt(T) of this row
         const double g = a.gbar ? a.gbar[i] : 1.0;
