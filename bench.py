@@ -45,8 +45,9 @@ BYTES_PER_ROW = 33 + 41
 # profiles/k_iv_binned_fwdbwd_stress.md.  Counts scale with the rows: every
 # launch of the same distribution does the same work per row on average.
 FLOPS_PER_ROW = 260.2
-# dram__bytes_read.sum + dram__bytes_write.sum per row from the same capture.
-TRAFFIC_PER_ROW = 132.7
+# dram__bytes_read.sum + dram__bytes_write.sum per row of the current kernel (one launch of
+# 4,194,304 stress rows, profiles/k_iv_binned_fwdbwd_stress.md).
+TRAFFIC_PER_ROW = 130.9
 # Executed FLOPs per row of the other measured forms, counted by ncu the same way on one launch
 # of 4,194,304 rows of each workload (python bench.py --case <name> --rows 4194304; FP32 from
 # smsp__sass_thread_inst_executed_op_{fadd,fmul}_pred_on + 2 x ..._ffma_pred_on), see
