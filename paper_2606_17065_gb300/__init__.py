@@ -9,9 +9,9 @@ from .api import (GATES, MODES, ROW_ABOVE_UPPER, ROW_AT_INTRINSIC, ROW_AT_UPPER,
                   ROW_BELOW_INTRINSIC, ROW_OK, BlackPrice, ImpliedVol, black_price, black_price_autograd,
                   black_price_backward, implied_volatility_autograd, iv, iv_backward, iv_forward_backward,
                   iv_guess, MlpTrainer, ImpliedVolBS, bs_implied_volatility_autograd, bs_iv, bs_iv_backward,
-                  bs_iv_forward_backward, bs_price, new_counters)
+                  bs_iv_forward_backward, bs_price, new_counters, release_host_buffers)
 
-__all__ = ["new_counters", "bs_price", "bs_iv", "bs_iv_backward", "bs_iv_forward_backward", "ImpliedVolBS",
+__all__ = ["new_counters", "release_host_buffers", "bs_price", "bs_iv", "bs_iv_backward", "bs_iv_forward_backward", "ImpliedVolBS",
            "bs_implied_volatility_autograd", "iv_guess", "MlpTrainer", "black_price", "black_price_backward", "BlackPrice", "black_price_autograd", "iv", "iv_backward", "iv_forward_backward", "ImpliedVol", "implied_volatility_autograd",
            "GATES", "MODES", "ROW_OK", "ROW_BELOW_INTRINSIC", "ROW_ABOVE_UPPER", "ROW_BAD_INPUT", "ROW_AT_INTRINSIC",
            "ROW_AT_UPPER"]

@@ -1206,12 +1206,13 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   const double y_tmh = itm ? E2 - yb : 0.0; // Y(t - h), in-the-money quotes only
   const double u1 = fle ? (call ? y_hpt : y_mhpt) : (call ? y_tmh : yb);  // Y(theta d1)
   const double u2 = fle ? (call ? yb : y_tmh) : (call ? y_mhpt : y_hpt);  // Y(theta d2)
-  const double sg = call ? 1.0 : -1.0;
-  const double rsq2 = rsq * rsq;
-  const double jP = ibs * rsq * inv_sqT; // 1/V, V = b_s sqrt(F K) sqrt(T)
-  const double jF = -sg * u1 * (K * rsq2) * inv_sqT;
-  const double jK = sg * u2 * (F * rsq2) * inv_sqT;
-  const double jT = -0.5 * sigma * inv_sqT * inv_sqT;
+  // with c = rsq / sqrt(T): 1/V = c / b_s, 1/(F sqrt T) = (K rsq) c, 1/(K sqrt T) = (F rsq) c;
+  // the signs go on the Mills ratios (a select, not a multiplication)
+  const double c = rsq * inv_sqT;
+  const double jP = ibs * c; // 1/V, V = b_s sqrt(F K) sqrt(T)
+  const double jF = (call ? -u1 : u1) * ((K * rsq) * c);
+  const double jK = (call ? u2 : -u2) * ((F * rsq) * c);
+  const double jT = (-0.5 * sigma) * (inv_sqT * inv_sqT);
   Grad out;
   const bool in_g = cmp_lt(tau * jP, 1.0); // V > tau
   if (mode == 0 || (mode <= 2 && in_g)) {
