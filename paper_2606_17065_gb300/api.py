@@ -129,7 +129,7 @@ def release_host_buffers():
 def _copy_streams(device):
     key = device.index
     if key not in _streams:
-        _streams[key] = tuple(torch.cuda.Stream(device) for _ in range(HOST_STREAMS))
+        _streams[key] = tuple(torch.cuda.Stream(device) for _ in range(max(2, HOST_STREAMS)))  # >= 1 compute + copy-out
     return _streams[key]
 
 

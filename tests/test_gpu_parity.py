@@ -307,8 +307,9 @@ def test_host_tensors_round_trip(body):
 
 @pytest.mark.parametrize("call", ["iv", "iv_forward_backward", "bs_iv", "bs_iv_forward_backward"])
 def test_host_chunked_pipeline_matches_device_path(monkeypatch, call):
-    """Host inputs above the chunk size are streamed in chunks over two streams; every output is
-    bit-identical to one call on device-resident inputs (ragged last chunk included)."""
+    """Host inputs above the chunk size are streamed in chunks (copy-in and kernel streams taking
+    turns, one copy-out stream); every output is bit-identical to one call on device-resident
+    inputs (ragged last chunk included)."""
     from paper_2606_17065_gb300 import api
     monkeypatch.setattr(api, "HOST_CHUNK", 4096)
     n = 3 * 4096 + 77
@@ -330,6 +331,27 @@ def test_host_chunked_pipeline_matches_device_path(monkeypatch, call):
     for g, w in zip(got, want):
         assert not g.is_cuda
         assert torch.equal(torch.nan_to_num(g.double(), nan=7.0), torch.nan_to_num(w.cpu().double(), nan=7.0))
+
+
+@pytest.mark.parametrize("streams", [2, 4, 5])
+def test_host_staging_reused_across_calls(monkeypatch, streams):
+    """The kept staging buffers and the copy-out stream: two different batches in a row, with
+    2 to 5 streams (1 to 4 copy-in/kernel streams), each give the device path's bits; after
+    release_host_buffers the next call allocates afresh and still matches."""
+    from paper_2606_17065_gb300 import api
+    monkeypatch.setattr(api, "HOST_CHUNK", 4096)
+    monkeypatch.setattr(api, "HOST_STREAMS", streams)
+    monkeypatch.setattr(api, "_streams", {})
+    for k, seed in enumerate((214, 215, 216)):
+        if k == 2:
+            pv.release_host_buffers()
+        n = 5 * 4096 + 13 * k
+        b = workloads.stress_batch(n, seed=seed)
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (b.F, b.K, b.T, oracle_inputs(b), b.flag)]
+        got = pv.iv_forward_backward(*host)
+        want = pv.iv_forward_backward(*[h.to(DEV) for h in host])
+        for g, w in zip(got, want):
+            assert torch.equal(torch.nan_to_num(g.double(), nan=7.0), torch.nan_to_num(w.cpu().double(), nan=7.0))
 
 
 def test_host_outputs_given_by_the_caller(monkeypatch):
