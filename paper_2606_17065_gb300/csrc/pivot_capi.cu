@@ -169,7 +169,8 @@ struct TileCfg {
   static constexpr int kThreads = 256;  // also the rows of a chunk
   static constexpr int kMinBlocks = 2;
   static constexpr int kCap = kBS ? (kMixed ? 1024 : 1280) : (kMixed ? 1536 : 1792);
-  static constexpr int kMaxPass = kCap / kThreads;  // chunks per phase-1 pass, rows per thread in phase 2
+  static constexpr int kMaxPass = kCap / kThreads;                 // chunks per phase-1 pass
+  static constexpr int kRows2 = (kCap + kThreads - 1) / kThreads;  // slots per thread in phase 2
   static constexpr int kSlots = kCarry + kCap;
   static constexpr size_t kSmem = size_t(kBS ? 8 : 6) * kSlots * sizeof(double) + size_t(kCarry) * sizeof(int64_t) +
                                   size_t(kSlots) * sizeof(uint16_t) + size_t(kCap) * sizeof(uint16_t) +
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
   using Cfg = TileCfg<kBS, kMixed>;
   constexpr int kThreads = Cfg::kThreads;
   constexpr int kMaxPass = Cfg::kMaxPass;
+  constexpr int kRows2 = Cfg::kRows2;
   constexpr int kCap = Cfg::kCap;
   constexpr int kBins = Cfg::kBins;
   constexpr int kCarry = Cfg::kCarry;
@@ -331,9 +333,9 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
     }
     const bool last = cursor >= nchunks;  // the block's last tile takes every row
     // ---- phase 2
-    int reg[kMaxPass], pos[kMaxPass], row[kMaxPass];
+    int reg[kRows2], pos[kRows2], row[kRows2];
 #pragma unroll
-    for (int j = 0; j < kMaxPass; ++j) {
+    for (int j = 0; j < kRows2; ++j) {
       const int qi = j * kThreads + tid;
       int rg = -1;
       row[j] = 0;
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kMaxPass; ++j) {
+    for (int j = 0; j < kRows2; ++j) {
       const int b = reg[j];
       if (b >= 0) {
         const int p = pos[j], full = s_full[b];

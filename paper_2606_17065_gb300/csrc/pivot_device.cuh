@@ -694,6 +694,24 @@ __device__ __forceinline__ R node_sl(R ax, float uf, R sc, R e) {
   return sc - R(kSqrtPiOver2) * (R(1) - e);
 }
 
+// exp(-a^2/2) and Phi(-a) = exp(-a^2/2) erfcx(a/sqrt 2) / 2 for a >= 0, as the lower and upper
+// guesses use them: they place a rational interpolation's end value and slope, so the FP64 form
+// takes them at float precision (~1e-7 relative, against the guess's ~1e-2 interpolation error)
+// while exp(-a^2/2) is a normal float (a < 9), and in FP64 beyond.
+template <typename R>
+__device__ __forceinline__ void seed_tail(R a, R& ea, R& Pa) {
+  using M = Math<R>;
+  if (sizeof(R) == 8 && cmp_lt(double(a), 9.0)) {
+    const float af = float(a);
+    const float e = ::expf(-0.5f * af * af);
+    ea = R(e);
+    Pa = R(0.5f * e * Math<float>::erfcx_half_(af));
+    return;
+  }
+  ea = M::exp_(R(-0.5) * a * a);
+  Pa = R(0.5) * ea * M::erfcx_half_(a);
+}
+
 template <typename R, bool kFastInv = true>
 __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbeta) {
   using M = Math<R>;
@@ -716,10 +734,11 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       R u = M::cbrt_(tiny ? v * M::kScaleUp : v) * (tiny ? M::kScaleDown : R(1));
       if (__builtin_expect(!gt0(v), 0)) u = M::exp_((lnbeta - M::log_(kap)) * R(1.0 / 3.0));
       const R ul = M::cbrt_(bl * inv_kap);
-      const R al = quot(ax * R(kInvSqrt3), sl);
+      // a_l only places the interpolation's end point: a float quotient in the FP64 form
+      const R al = sizeof(R) == 8 ? R(float(ax) * float(kInvSqrt3) / float(sl)) : quot(ax * R(kInvSqrt3), sl);
       // Phi(-al) = phi(al) Y(-al) = exp(-al^2/2) erfcx(al/sqrt 2) / 2: one exponential shared with phi(al)
-      const R eal = M::exp_(R(-0.5) * al * al);
-      const R Gl = R(0.5) * eal * M::erfcx_half_(al);
+      R eal, Gl;
+      seed_tail<R>(al, eal, Gl);
       const R dGl = quot(R(3) * bl * (R(kInvSqrt2Pi) * eal) * al, sl * ul * bsl);
       const R r = shape_monotone<R>(ul, R(0), Gl, R(1), dGl);
       const R G = M::fmin_(rational_cubic<R>(u, R(0), ul, R(0), Gl, R(1), dGl, r), R(0.5));
@@ -755,8 +774,8 @@ __device__ __forceinline__ R region_guess(int region, const Node<R>& nd, R lnbet
       const R su = sc + R(kSqrtPiOver2) * (R(1) + e);
       const R uu = R(0.5) * nd.bn;
       // Phi(-su/2) and phi(su/2) from one exponential, as in the lower region
-      const R esu = M::exp_(R(-0.125) * su * su);
-      const R vu = R(0.5) * esu * M::erfcx_half_(R(0.5) * su);
+      R esu, vu;
+      seed_tail<R>(R(0.5) * su, esu, vu);
       const R dvu = quot(R(kInvSqrt2Pi) * esu, nd.bsn);
       const R r = shape_monotone<R>(uu, R(0), vu, R(1), dvu);
       const R v = M::fmin_(rational_cubic<R>(R(0.5) * nd.bb, R(0), uu, R(0), vu, R(1), dvu, r), R(0.5));
