@@ -259,6 +259,29 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
       // a pass costs a round trip to memory and two barriers: none for a single chunk once the
       // tile holds rows (mixed stress 3.00 -> 2.97 ms)
       if (take < 2 && nch > 0) break;
+      // the pass's loads first, all in flight at once: the stores of one row's outputs would
+      // otherwise keep the next row's loads behind them (the output arrays may alias the inputs
+      // as far as the compiler knows), one memory round trip per chunk instead of per pass
+      double rF[kMaxPass], rK[kMaxPass], rT[kMaxPass], rP[kMaxPass], rr[kBS ? kMaxPass : 1], rq[kBS ? kMaxPass : 1];
+      int rfl[kMaxPass];
+#pragma unroll
+      for (int j = 0; j < kMaxPass; ++j) {
+        const int64_t i = (cursor + int64_t(j) * gridDim.x) * kThreads + tid;
+        rF[j] = rK[j] = rT[j] = rP[j] = 0.0;
+        rfl[j] = 0;
+        if (kBS) rr[kBS ? j : 0] = rq[kBS ? j : 0] = 0.0;
+        if (j < take && i < a.n) {
+          rF[j] = a.F[i];
+          rK[j] = a.K[i];
+          rT[j] = a.T[i];
+          rP[j] = a.P[i];
+          rfl[j] = a.flag[i];
+          if (kBS) {
+            rr[kBS ? j : 0] = a.r[i];
+            rq[kBS ? j : 0] = a.q[i];
+          }
+        }
+      }
 #pragma unroll
       for (int j = 0; j < kMaxPass; ++j) {
         if (j >= take) break;  // uniform over the block
@@ -269,14 +292,14 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         int row_status = -1;
         double tv = 0.0, cv = 0.0, er = 1.0, ec = 1.0, Fs = 0.0, Ks = 0.0;
         if (i < a.n) {
-          const double K = a.K[i], T = a.T[i];
-          double F = a.F[i], P = a.P[i];
+          const double K = rK[j], T = rT[j];
+          double F = rF[j], P = rP[j];
           if (kBS) {
-            pivot::bs_factors(T, a.r[i], a.q[i], er, ec);
+            pivot::bs_factors(T, rr[kBS ? j : 0], rq[kBS ? j : 0], er, ec);
             F *= ec;
             P *= er;
           }
-          const int fl = a.flag[i];
+          const int fl = rfl[j];
           const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
           row_status = q.status;
           // every row's status here, in row order (a solved row's stays 0): one coalesced byte
