@@ -120,7 +120,23 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       for (int k = 0; k < kIBins; ++k) S.cnt[k] = 0;
     }
     __syncthreads();
-    // ---- phase 1
+    // ---- phase 1: every row's loads first (a row's output stores would otherwise hold the
+    // next row's loads back), then the stage-1 tests
+    double rF[kIRowsPerThread], rK[kIRowsPerThread], rT[kIRowsPerThread], rP[kIRowsPerThread];
+    int rfl[kIRowsPerThread];
+#pragma unroll
+    for (int j = 0; j < kIRowsPerThread; ++j) {
+      const int64_t i = base + j * kIBlock + tid;
+      rF[j] = rK[j] = rT[j] = rP[j] = 0.0;
+      rfl[j] = 0;
+      if (i < a.n) {
+        rF[j] = a.F[i];
+        rK[j] = a.K[i];
+        rT[j] = a.T[i];
+        rP[j] = a.P[i];
+        rfl[j] = a.flag[i];
+      }
+    }
 #pragma unroll
     for (int j = 0; j < kIRowsPerThread; ++j) {
       const int r = j * kIBlock + tid;
@@ -128,8 +144,8 @@ __global__ void __launch_bounds__(kIBlock, 2) k_iv_learned(Args a, const pivot_m
       bool solve = false;
       int row_status = -1;
       if (i < a.n) {
-        const double F = a.F[i], K = a.K[i], T = a.T[i], P = a.P[i];
-        const int fl = a.flag[i];
+        const double F = rF[j], K = rK[j], T = rT[j], P = rP[j];
+        const int fl = rfl[j];
         const pivot::Quote q = pivot::classify_quote(F, K, T, P, fl);
         row_status = q.status;
         if (q.status != 0) {
