@@ -2,8 +2,8 @@
 exponential in pivot_device.cuh (P. T. P. Tang's method: ACM TOMS 15(2), 1989, for exp;
 16(4), 1990, for log), written for this library.
 
-log: v = 2^e m, m in [1, 2), c_j = 1 + j/128 with j = round(128 (m - 1)) in [0, 128];
-     ln v = e ln 2 + ln c_j + ln(1 + f), f = (m - c_j)/c_j, |f| <= 1/256.
+log: v = 2^e m, m in [1, 2), c_j = 1 + j/1024 with j = round(1024 (m - 1)) in [0, 1024];
+     ln v = e ln 2 + ln c_j + ln(1 + f), f = (m - c_j)/c_j, |f| <= 1/2048.
      Tables: 1/c_j, and ln c_j split as hi + lo with hi a multiple of 2^-43, so that
      e ln2_hi + ln c_j hi is exact for every exponent e.
 exp: v = (128 n' + k) ln2/128 + r, |r| <= ln2/256; e^v = 2^n' 2^(k/128) e^r.
@@ -16,6 +16,8 @@ import os
 
 import mpmath as mp
 
+LOG_N = 1024  # log table: c_j = 1 + j/LOG_N, j = 0..LOG_N
+
 
 def split43(v):
     """v = hi + lo with hi a multiple of 2^-43 (|v| < 1): hi has at most ~43 significant bits."""
@@ -26,8 +28,8 @@ def split43(v):
 def main():
     mp.mp.dps = 50
     inv_c, lnc_hi, lnc_lo = [], [], []
-    for j in range(129):
-        c = 1 + mp.mpf(j) / 128
+    for j in range(LOG_N + 1):
+        c = 1 + mp.mpf(j) / LOG_N
         inv_c.append(float(1 / c))
         hi, lo = split43(mp.log(c))
         lnc_hi.append(hi)
@@ -49,11 +51,11 @@ def main():
         fh.write(f"static constexpr double kLn2By128Hi = {float(l_hi)!r};\n")
         fh.write(f"static constexpr double kLn2By128Lo = {float(l - l_hi)!r};\n")
         fh.write(f"static constexpr double k128ByLn2 = {float(128 / mp.log(2))!r};\n")
-        fh.write("static __device__ const double kLogInvC[129] = {\n")
+        fh.write(f"static __device__ const double kLogInvC[{LOG_N + 1}] = {{\n")
         fh.write("".join(f"    {v!r},\n" for v in inv_c))
-        fh.write("};\nstatic __device__ const double kLogCHi[129] = {\n")
+        fh.write(f"}};\nstatic __device__ const double kLogCHi[{LOG_N + 1}] = {{\n")
         fh.write("".join(f"    {v!r},\n" for v in lnc_hi))
-        fh.write("};\nstatic __device__ const double kLogCLo[129] = {\n")
+        fh.write(f"}};\nstatic __device__ const double kLogCLo[{LOG_N + 1}] = {{\n")
         fh.write("".join(f"    {v!r},\n" for v in lnc_lo))
         fh.write("};\nstatic __device__ const double kExp2Hi[128] = {\n")
         fh.write("".join(f"    {v!r},\n" for v in exp_hi))

@@ -36,12 +36,12 @@ def dlog(v, t, c):
     b = v.view(np.int64)
     e = ((b >> 52) & 0x7ff) - 1023
     m = ((b & 0x000fffffffffffff) | (1023 << 52)).view(np.float64)
-    tr = fma(m - 1.0, 128.0, MAGIC)
-    j = tr.view(np.int64) & 0xff
+    tr = fma(m - 1.0, 1024.0, MAGIC)
+    j = tr.view(np.int64) & 0x7ff
     jd = tr - MAGIC
-    f = (m - fma(jd, 0.0078125, 1.0)) * t["kLogInvC"][j]
-    q = np.full_like(f, 1.0 / 7.0)
-    for k in (-1.0 / 6.0, 0.2, -0.25, 1.0 / 3.0, -0.5, 1.0):
+    f = (m - fma(jd, 0.0009765625, 1.0)) * t["kLogInvC"][j]
+    q = np.full_like(f, 0.2)
+    for k in (-0.25, 1.0 / 3.0, -0.5, 1.0):
         q = fma(q, f, k)
     ed = e.astype(np.float64)
     hi = fma(ed, c["kLn2Hi"], t["kLogCHi"][j])
@@ -68,8 +68,9 @@ def dexp(v, t, c):
 def test_tables_against_mpmath():
     t, c = _tables()
     mp.mp.dps = 40
-    for j in range(129):
-        cj = 1 + mp.mpf(j) / 128
+    assert len(t["kLogInvC"]) == len(t["kLogCHi"]) == len(t["kLogCLo"]) == 1025
+    for j in range(1025):
+        cj = 1 + mp.mpf(j) / 1024
         assert t["kLogInvC"][j] == float(1 / cj)
         # hi + lo within the rounding of lo
         assert abs(mp.mpf(t["kLogCHi"][j]) + mp.mpf(t["kLogCLo"][j]) - mp.log(cj)) <= abs(t["kLogCLo"][j]) * 2.0 ** -52 + mp.mpf(2) ** -120
@@ -88,6 +89,9 @@ def test_method_within_one_ulp():
     mp.mp.dps = 40
     rng = np.random.default_rng(0)
     v = np.concatenate([10.0 ** rng.uniform(-300, 300, 400), 1 + rng.uniform(-1e-3, 1e-3, 200),
+                        # each side of every 32nd table node (the reduction's rounding boundaries)
+                        (1 + (np.arange(0, 1025, 32) + 0.5) / 1024) * np.array([1.0]).repeat(33),
+                        (1 + (np.arange(0, 1025, 32) - 0.5) / 1024)[1:],
                         1 + rng.uniform(-1e-13, 1e-13, 100), rng.uniform(0.5, 2.0, 200),
                         np.array([1.0, 2.0, 0.5, np.nextafter(1.0, 0.0), np.nextafter(1.0, 2.0), 2.2250738585072014e-308])])
     got = dlog(v, t, c)
