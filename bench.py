@@ -44,23 +44,23 @@ BYTES_PER_ROW = 33 + 41
 # over one launch of 4,194,304 stress rows, divided by the rows), see
 # profiles/k_iv_binned_fwdbwd_stress.md.  Counts scale with the rows: every
 # launch of the same distribution does the same work per row on average.
-FLOPS_PER_ROW = 260.0
+FLOPS_PER_ROW = 236.7
 # dram__bytes_read.sum + dram__bytes_write.sum per row of the current kernel (one launch of
 # 4,194,304 stress rows, profiles/k_iv_binned_fwdbwd_stress.md).
-TRAFFIC_PER_ROW = 125.5
+TRAFFIC_PER_ROW = 125.6
 # Executed FLOPs per row of the other measured forms, counted by ncu the same way on one launch
 # of 4,194,304 rows of each workload (python bench.py --case <name> --rows 4194304; FP32 from
 # smsp__sass_thread_inst_executed_op_{fadd,fmul}_pred_on + 2 x ..._ffma_pred_on), see
 # profiles/flops_per_row_all_forms.md.
 FLOPS = {
     # case: (FP64 FLOP / row, FP32 FLOP / row)
-    "stress": (FLOPS_PER_ROW, 51.4),
-    "stress-mixed": (96.4, 231.9),
-    "body": (533.7, 102.7),
-    "body-mixed": (223.9, 508.9),
-    "body-learned": (223.1, 1589.0),
-    "bs-wide": (349.9, 60.9),
-    "bs-wide-mixed": (159.4, 271.9),
+    "stress": (FLOPS_PER_ROW, 72.6),
+    "stress-mixed": (94.6, 232.0),
+    "body": (507.7, 124.4),
+    "body-mixed": (219.9, 508.9),
+    "body-learned": (219.2, 1589.0),
+    "bs-wide": (322.3, 86.2),
+    "bs-wide-mixed": (157.3, 272.1),
 }
 # MLP inference of the learned seed, 2 -> 64 -> 64 -> 64 -> 1: 2 (2 64 + 64 64 + 64 64 + 64) FLOP
 # per seeded row on the BF16 tensor cores (algorithmic count)
