@@ -197,9 +197,26 @@ __device__ __forceinline__ void row_fp(const Args& a, int64_t i, int r, const do
   }
 }
 
-template <bool kBackward, bool kMixed, bool kBS>
+// kSmall: chunks of a.chunk_rows < kThreads rows, so that a small batch spreads over more
+// blocks; a separate instantiation with its own argument type, so that the full-chunk kernels
+// of large batches keep their code and their parameters
+struct ArgsChunked : Args {
+  int chunk_rows; // 32..kThreads, a multiple of 32
+};
+template <bool kSmall>
+struct BinnedArgs {
+  using type = Args;
+};
+template <>
+struct BinnedArgs<true> {
+  using type = ArgsChunked;
+};
+__device__ __forceinline__ int chunk_rows_of(const Args&, int full) { return full; }
+__device__ __forceinline__ int chunk_rows_of(const ArgsChunked& a, int) { return a.chunk_rows; }
+
+template <bool kBackward, bool kMixed, bool kBS, bool kSmall = false>
 __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, kMixed>::kMinBlocks)
-    k_iv_binned(Args a) {
+    k_iv_binned(typename BinnedArgs<kSmall>::type a) {
   using Cfg = TileCfg<kBS, kMixed>;
   constexpr int kThreads = Cfg::kThreads;
   constexpr int kMaxPass = Cfg::kMaxPass;
@@ -241,7 +258,11 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
     const int c = s_code[r - kCarry];
     return s_cbase[c >> 8] + (c & 0xff);
   };
-  const int64_t nchunks = (a.n + kThreads - 1) / kThreads;
+  // rows per chunk: kThreads, or fewer (a multiple of 32) on a batch too small to give every
+  // resident block a full chunk; threads at or beyond it take no row in phase 1
+  const int crows = chunk_rows_of(a, kThreads);
+  const bool has_row = !kSmall || tid < crows;
+  const int64_t nchunks = (a.n + crows - 1) / crows;
   int64_t cursor = blockIdx.x;  // this block's next chunk
   if (tid < kBins) s_ccnt[tid] = 0;
   while (cursor < nchunks) {
@@ -266,7 +287,7 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
       int rfl[kMaxPass];
 #pragma unroll
       for (int j = 0; j < kMaxPass; ++j) {
-        const int64_t i = (cursor + int64_t(j) * gridDim.x) * kThreads + tid;
+        const int64_t i = has_row ? (cursor + int64_t(j) * gridDim.x) * crows + tid : a.n;
         rF[j] = rK[j] = rT[j] = rP[j] = 0.0;
         rfl[j] = 0;
         if (kBS) rr[kBS ? j : 0] = rq[kBS ? j : 0] = 0.0;
@@ -286,8 +307,8 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
       for (int j = 0; j < kMaxPass; ++j) {
         if (j >= take) break;  // uniform over the block
         const int64_t c = cursor + int64_t(j) * gridDim.x;
-        const int64_t i = c * kThreads + tid;
-        if (tid == 0 && c < nchunks) s_cbase[nch + j] = c * kThreads;
+        const int64_t i = has_row ? c * crows + tid : a.n;
+        if (tid == 0 && c < nchunks) s_cbase[nch + j] = c * crows;
         bool solve = false;
         int row_status = -1;
         double tv = 0.0, cv = 0.0, er = 1.0, ec = 1.0, Fs = 0.0, Ks = 0.0;
@@ -592,29 +613,48 @@ int check_opts(const pivot_opts* o, int* steps, int* mode) {
 }
 
 // persistent grid for the binned kernels: resident blocks x SMs, capped by the chunks
-template <bool kBackward, bool kMixed, bool kBS = false>
-int launch_binned(const Args& a, void* stream) {
+template <bool kBackward, bool kMixed, bool kBS, bool kSmall>
+int launch_binned_as(const Args& a, int64_t crows, void* stream) {
   // occupancy of this instantiation, looked up once per device
   static thread_local int configured_device = -1;
-  static thread_local int blocks_per_sm = 0, num_sms = 0;
+  static thread_local int64_t cap = 0;
   constexpr size_t smem = TileCfg<kBS, kMixed>::kSmem;
   constexpr int kThreads = TileCfg<kBS, kMixed>::kThreads;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return launch_status();
   if (configured_device != dev) {
-    const void* f = reinterpret_cast<const void*>(k_iv_binned<kBackward, kMixed, kBS>);
+    const void* f = reinterpret_cast<const void*>(k_iv_binned<kBackward, kMixed, kBS, kSmall>);
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    int b = 0;
+    int b = 0, num_sms = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kThreads, smem);
     cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    blocks_per_sm = b < 1 ? 1 : b;
+    cap = int64_t(b < 1 ? 1 : b) * num_sms;
     configured_device = dev;
   }
-  const int64_t cap = int64_t(blocks_per_sm) * num_sms;
-  const int64_t chunks = (a.n + kThreads - 1) / kThreads;  // every block gets at least one
+  if (crows <= 0) {
+    // rows per chunk: a full block's worth, or on a small batch the multiple of 32 that spreads
+    // it over up to every resident block (a 4,096-row batch: 128 blocks of 32 rows, not 16 of 256)
+    crows = (a.n + cap - 1) / cap;
+    crows = ((crows + 31) / 32) * 32;
+    if (crows > kThreads) crows = kThreads;
+    if (crows < 32) crows = 32;
+    if (crows < kThreads) return launch_binned_as<kBackward, kMixed, kBS, true>(a, crows, stream);
+  }
+  const int64_t chunks = (a.n + crows - 1) / crows;  // every block gets at least one
   const unsigned grid = unsigned(chunks < cap ? chunks : cap);
-  k_iv_binned<kBackward, kMixed, kBS><<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(a);
+  if (kSmall) {
+    ArgsChunked b;
+    static_cast<Args&>(b) = a;
+    b.chunk_rows = int(crows);
+    k_iv_binned<kBackward, kMixed, kBS, true><<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(b);
+  } else {
+    k_iv_binned<kBackward, kMixed, kBS, false><<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(a);
+  }
   return launch_status();
+}
+template <bool kBackward, bool kMixed, bool kBS = false>
+int launch_binned(const Args& a, void* stream) {
+  return launch_binned_as<kBackward, kMixed, kBS, false>(a, 0, stream);
 }
 
 }  // namespace
