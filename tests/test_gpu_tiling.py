@@ -137,3 +137,23 @@ def test_sparse_solves_fill_tiles_from_many_chunks(mode):
                               where=f"sparse {mode}")
     want = oracle.iv_grad(sb.F, sb.K, sb.T, sb.flag, ref, None, 1e-6, 1, nthreads=0)
     assert_grad_parity([to_np(g[sel]) for g in whole[2:]], want, dom, where=f"sparse {mode}")
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_small_batch_chunks_match_full_chunks(mode):
+    """Batches too small for a 256-row chunk per resident block run a separate kernel
+    instantiation with 32- to 224-row chunks.  Rows are solved independently of their chunk and
+    tile, so each small batch gives, bit for bit, what the same rows give inside a large batch
+    run with full chunks; the sizes cover several chunk sizes and ragged ends."""
+    n_big = 400_000
+    b = workloads.stress_batch(n_big, seed=37)
+    big = [to_dev(a) for a in (b.F, b.K, b.T, oracle_inputs(b), b.flag)]
+
+    def run(F, K, T, P, flag):
+        return pv.iv_forward_backward(F, K, T, P, flag, tau=1e-6, gate="nan", mode=mode)
+
+    whole = run(*big)
+    for n in (1, 33, 4_096, 9_001, 40_000, 77_823):
+        part = run(*[t[:n].contiguous() for t in big])
+        torch.cuda.synchronize()
+        assert_same_bits(part, [w[:n] for w in whole], f"{mode} {n} rows vs the same rows in {n_big}")
