@@ -552,9 +552,13 @@ __global__ void __launch_bounds__(TileCfg<kBS, kMixed>::kThreads, TileCfg<kBS, k
         // the adjoint at the solved s, reusing x and 1/sqrt(T) of this row
         const double g = a.gbar ? a.gbar[i] : 1.0;
         const double gate_tau = kBS ? a.tau * s_er[r] : a.tau;  // G_tau on the cash vega e^{-r tau} V
-        const pivot::Grad d = pivot::nan64(g) ? pivot::degenerate_grad(true, g, a.mode)
-                                       : pivot::adjoint_reuse(F, K, fl, sig, s, s_x[r], bmax, inv_sqT, rsq, g,
-                                                              gate_tau, a.mode, last);
+        // (no gbar: the same launch-uniform branch on every row, and no products by 1)
+        const pivot::Grad d =
+            pivot::nan64(g) ? pivot::degenerate_grad(true, g, a.mode)
+            : a.gbar ? pivot::adjoint_reuse<false>(F, K, fl, sig, s, s_x[r], bmax, inv_sqT, rsq, g, gate_tau, a.mode,
+                                                   last)
+                     : pivot::adjoint_reuse<true>(F, K, fl, sig, s, s_x[r], bmax, inv_sqT, rsq, g, gate_tau, a.mode,
+                                                  last);
         if (kBS) {
           const pivot::BSGrad o = pivot::bs_grad(d, F, K, T, a.r[i], a.q[i], s_er[r], s_ec[r]);
           if (a.dP) a.dP[i] = o.dV;

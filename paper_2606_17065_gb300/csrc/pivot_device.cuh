@@ -1188,7 +1188,9 @@ __device__ __forceinline__ double mills_shift(double y0, double z0, double d) {
 // and the four quote types need (theta = flag):
 //   F <= K: d1 = h + t, d2 = h - t;  F > K: d1 = t - h, d2 = -(h + t);
 //   dsigma/dF uses Y(theta d1), dsigma/dK uses Y(theta d2).
-// 1/V = (1/b_s) rsq / sqrt(T) needs no division.
+// 1/V = (1/b_s) rsq / sqrt(T) needs no division.  kUnitG: the upstream gradient is 1 on every
+// row (no gbar), so the products by g are left out (x * 1 = x for every double, NaN included).
+template <bool kUnitG = false>
 __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, double sigma, double s, double x,
                                               double bmax, double inv_sqT, double rsq, double g, double tau, int mode,
                                               const Last& last) {
@@ -1235,10 +1237,10 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   Grad out;
   const bool in_g = cmp_lt(tau * jP, 1.0); // V > tau
   if (mode == 0 || (mode <= 2 && in_g)) {
-    out.dP = g * jP;
-    out.dF = g * jF;
-    out.dK = g * jK;
-    out.dT = g * jT;
+    out.dP = kUnitG ? jP : g * jP;
+    out.dF = kUnitG ? jF : g * jF;
+    out.dK = kUnitG ? jK : g * jK;
+    out.dT = kUnitG ? jT : g * jT;
     return out;
   }
   if (mode == 1) {
@@ -1263,10 +1265,10 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
     w = r * r * den;
     wP = r * inv_tau * den;
   }
-  out.dP = g * wP;
-  out.dF = g * jF * w;
-  out.dK = g * jK * w;
-  out.dT = g * jT * w;
+  out.dP = kUnitG ? wP : g * wP;
+  out.dF = (kUnitG ? jF : g * jF) * w;
+  out.dK = (kUnitG ? jK : g * jK) * w;
+  out.dT = (kUnitG ? jT : g * jT) * w;
   return out;
 }
 

@@ -95,8 +95,10 @@ __device__ __forceinline__ void finish_row(const Args& a, int64_t i, double F, d
   if (kBackward) {
     const double g = a.gbar ? a.gbar[i] : 1.0;
     const pivot::Grad d = isnan(g) ? pivot::degenerate_grad(true, g, a.mode)
-                                   : pivot::adjoint_reuse(F, K, fl, sig, s, x, bmax, inv_sqT, rsq, g,
-                                                          a.tau, a.mode, last);
+                          : a.gbar ? pivot::adjoint_reuse<false>(F, K, fl, sig, s, x, bmax, inv_sqT, rsq, g, a.tau,
+                                                                 a.mode, last)
+                                   : pivot::adjoint_reuse<true>(F, K, fl, sig, s, x, bmax, inv_sqT, rsq, g, a.tau,
+                                                                a.mode, last);
     if (a.dP) a.dP[i] = d.dP;
     if (a.dF) a.dF[i] = d.dF;
     if (a.dK) a.dK[i] = d.dK;
