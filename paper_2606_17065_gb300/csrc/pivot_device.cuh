@@ -1212,8 +1212,9 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   } else {
     ibs = exp_fp64(-lbs);
   }
-  // 1/b_max = max(F, K) rsq
-  double E1 = bmax * ibs, E2 = ibs * ((gt_pos(F, K) ? F : K) * rsq);
+  // 1/b_max = max(F, K) rsq (b_max = min(F, K) rsq, as the caller formed it)
+  const double inv_bmax = (gt_pos(F, K) ? F : K) * rsq;
+  double E1 = bmax * ibs, E2 = ibs * inv_bmax;
   if (!finite64(ibs)) {
     // b_s underflows (|ln(F/K)| beyond ~1400): the reflections from their own exponents
     E1 = kSqrt2Pi * exp_fp64(0.5 * hpt * hpt);
@@ -1227,12 +1228,13 @@ __device__ __forceinline__ Grad adjoint_reuse(double F, double K, int flag, doub
   const double y_tmh = itm ? E2 - yb : 0.0; // Y(t - h), in-the-money quotes only
   const double u1 = fle ? (call ? y_hpt : y_mhpt) : (call ? y_tmh : yb);  // Y(theta d1)
   const double u2 = fle ? (call ? yb : y_tmh) : (call ? y_mhpt : y_hpt);  // Y(theta d2)
-  // with c = rsq / sqrt(T): 1/V = c / b_s, 1/(F sqrt T) = (K rsq) c, 1/(K sqrt T) = (F rsq) c;
-  // the signs go on the Mills ratios (a select, not a multiplication)
+  // with c = rsq / sqrt(T): 1/V = c / b_s, 1/(F sqrt T) = (K rsq) c, 1/(K sqrt T) = (F rsq) c,
+  // where K rsq and F rsq are b_max and 1/b_max in some order (the same products); the signs go
+  // on the Mills ratios (a select, not a multiplication)
   const double c = rsq * inv_sqT;
   const double jP = ibs * c; // 1/V, V = b_s sqrt(F K) sqrt(T)
-  const double jF = (call ? -u1 : u1) * ((K * rsq) * c);
-  const double jK = (call ? u2 : -u2) * ((F * rsq) * c);
+  const double jF = (call ? -u1 : u1) * ((fle ? inv_bmax : bmax) * c);
+  const double jK = (call ? u2 : -u2) * ((fle ? bmax : inv_bmax) * c);
   const double jT = (-0.5 * sigma) * (inv_sqT * inv_sqT);
   Grad out;
   const bool in_g = cmp_lt(tau * jP, 1.0); // V > tau
