@@ -44,7 +44,7 @@ BYTES_PER_ROW = 33 + 41
 # over one launch of 4,194,304 stress rows, divided by the rows), see
 # profiles/k_iv_binned_fwdbwd_stress.md.  Counts scale with the rows: every
 # launch of the same distribution does the same work per row on average.
-FLOPS_PER_ROW = 236.7
+FLOPS_PER_ROW = 235.1
 # dram__bytes_read.sum + dram__bytes_write.sum per row of the current kernel (one launch of
 # 4,194,304 stress rows, profiles/k_iv_binned_fwdbwd_stress.md).
 TRAFFIC_PER_ROW = 125.6
@@ -55,12 +55,12 @@ TRAFFIC_PER_ROW = 125.6
 FLOPS = {
     # case: (FP64 FLOP / row, FP32 FLOP / row)
     "stress": (FLOPS_PER_ROW, 72.6),
-    "stress-mixed": (94.6, 232.0),
-    "body": (507.7, 124.4),
-    "body-mixed": (219.9, 508.9),
-    "body-learned": (219.2, 1589.0),
-    "bs-wide": (322.3, 86.2),
-    "bs-wide-mixed": (157.3, 272.1),
+    "stress-mixed": (93.0, 232.0),
+    "body": (502.0, 124.4),
+    "body-mixed": (214.2, 508.9),
+    "body-learned": (213.5, 1589.0),
+    "bs-wide": (320.5, 86.2),
+    "bs-wide-mixed": (155.6, 272.1),
 }
 # MLP inference of the learned seed, 2 -> 64 -> 64 -> 64 -> 1: 2 (2 64 + 64 64 + 64 64 + 64) FLOP
 # per seeded row on the BF16 tensor cores (algorithmic count)
