@@ -110,6 +110,33 @@ def test_forward_backward_fused_parity(body, stress):
         assert np.array_equal(sig, sig2, equal_nan=True)
 
 
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+@pytest.mark.parametrize("gate", [0, 1, 2, 3])
+def test_fused_with_upstream_gradient(body, stress, form, gate):
+    """The fused kernels with an upstream gradient gbar (their own adjoint instantiation: the
+    products by g kept), every gate, zeros and a NaN among the cotangents: against the oracle's
+    VJP with the same cotangents on the parity domain; and with g = 1 on every row, the same bits
+    as the call without gbar in the gates where g multiplies the result last."""
+    for name, (b, P, ref, st_ref) in (("body", body), ("stress", stress)):
+        rng = np.random.default_rng(50 + gate)
+        g = rng.normal(size=b.n)
+        g[::7] = 0.0
+        g[3] = np.nan
+        _, Vr = oracle.black_price(b.F, b.K, b.T, np.where(np.isfinite(ref), ref, 1.0), b.flag, nthreads=0)
+        tau = float(np.median(Vr[st_ref == 0])) * 0.1
+        args = [to_dev(a) for a in (b.F, b.K, b.T, P, b.flag)]
+        sig, st, *grads = [to_np(x) for x in pv.iv_forward_backward(*args, to_dev(g), tau=tau, gate=gate, mode=form)]
+        dom = assert_sigma_parity(b.F, b.K, b.T, P, b.flag, sig, st, ref, st_ref, where=f"gbar {form} {name}")
+        want = oracle.iv_grad(b.F, b.K, b.T, b.flag, ref, g, tau, gate, nthreads=0)
+        assert_grad_parity(grads, want, dom, where=f"gbar {form} {name} gate={gate}", vega=Vr, gbar=g)
+        if gate != 3:
+            ones = [to_np(x) for x in pv.iv_forward_backward(*args, to_dev(np.ones(b.n)), tau=tau, gate=gate,
+                                                              mode=form)]
+            none = [to_np(x) for x in pv.iv_forward_backward(*args, tau=tau, gate=gate, mode=form)]
+            for x, y in zip(ones, none):
+                assert np.array_equal(x, y, equal_nan=True), f"gbar = 1 vs no gbar, {form} {name} gate={gate}"
+
+
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
 def test_fused_gradients_off_parity_domain(body, stress, mode):
     """The fused kernels' adjoint (the last Householder evaluation's Mills ratios reused) on

@@ -153,7 +153,26 @@ def test_small_batch_chunks_match_full_chunks(mode):
         return pv.iv_forward_backward(F, K, T, P, flag, tau=1e-6, gate="nan", mode=mode)
 
     whole = run(*big)
+    fwd_whole = pv.iv(*big, mode=mode)
     for n in (1, 33, 4_096, 9_001, 40_000, 77_823):
-        part = run(*[t[:n].contiguous() for t in big])
+        sub = [t[:n].contiguous() for t in big]
+        part = run(*sub)
+        fwd = pv.iv(*sub, mode=mode)
         torch.cuda.synchronize()
         assert_same_bits(part, [w[:n] for w in whole], f"{mode} {n} rows vs the same rows in {n_big}")
+        assert_same_bits(fwd, [w[:n] for w in fwd_whole], f"{mode} forward {n} rows vs the same rows in {n_big}")
+
+
+def test_small_black_scholes_batch_matches_full_chunks():
+    """The same for the Black-Scholes form (its own kernel instantiations)."""
+    n_big = 400_000
+    b = workloads.bs_batch(n_big, seed=38, wide=True)
+    d = [to_dev(a) for a in (b.S, b.K, b.T, b.r, b.q, b.sigma_star)]
+    fl = to_dev(b.flag)
+    V, _ = pv.bs_price(*d, fl, vega=False)
+    args = (*d[:5], V.contiguous(), fl)
+    whole = pv.bs_iv_forward_backward(*args, tau=1e-6, gate="nan")
+    for n in (57, 9_001, 77_823):
+        part = pv.bs_iv_forward_backward(*[t[:n].contiguous() for t in args], tau=1e-6, gate="nan")
+        torch.cuda.synchronize()
+        assert_same_bits(part, [w[:n] for w in whole], f"Black-Scholes {n} rows vs the same rows in {n_big}")
