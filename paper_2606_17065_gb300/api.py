@@ -86,9 +86,19 @@ HOST_RAMP = True
 _streams = {}
 
 
-def _chunks(n):
-    """(start, rows) of the chunks of an n-row host call."""
-    C = HOST_CHUNK
+def _host_chunk(n):
+    """Rows per chunk of an n-row host call, or 0 for one unpipelined round trip: HOST_CHUNK on
+    large calls; a quarter of the call (at least HOST_CHUNK / 8) down to HOST_CHUNK / 4 rows, so
+    that mid-size calls overlap their copies with the kernels too; below that, 0."""
+    if n <= HOST_CHUNK // 4:
+        return 0
+    return min(HOST_CHUNK, max(HOST_CHUNK // 8, -(-n // 4)))
+
+
+def _chunks(n, C=None):
+    """(start, rows) of the chunks of an n-row host call, C rows each (_host_chunk(n), or
+    HOST_CHUNK where n is too small to pipeline)."""
+    C = C or _host_chunk(n) or HOST_CHUNK
     sizes = [min(C, n - lo) for lo in range(0, n, C)]
     if HOST_RAMP and len(sizes) >= 3 and C >= 64:
         head = [C // 8, C // 8, C // 4, C - C // 8 - C // 8 - C // 4]
@@ -170,20 +180,21 @@ def _check_out(out, n, dtypes):
 def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args, out=None):
     """Run one row-wise entry point.  `build_args(m, ins, outs)` returns its
     arguments for m rows of device tensors, stream excluded.  Device inputs
-    run in place on the current stream; host inputs larger than HOST_CHUNK are
-    pipelined chunk by chunk (host -> device, kernel, device -> host on
-    rotating streams) into pinned host outputs, the caller's (`out`, host
-    inputs only) or new ones."""
+    run in place on the current stream; host inputs of more than HOST_CHUNK / 4
+    rows are pipelined chunk by chunk (host -> device and kernel on rotating
+    streams, device -> host on a stream of its own) into pinned host outputs,
+    the caller's (`out`, host inputs only) or new ones."""
     n = next(t for t in inputs if t is not None)
     n = n.numel() if isinstance(n, torch.Tensor) else len(n)
     if out is not None and not _is_host(inputs):
         raise ValueError("out is for host inputs only")
-    if out is not None and n <= HOST_CHUNK:
+    C = _host_chunk(n) if _is_host(inputs) else 0
+    if out is not None and C == 0:
         res = _rows_call(name, inputs, in_dtypes, out_dtypes, build_args)
         for o, r in zip(_check_out(out, n, out_dtypes), res):
             o.copy_(r)
         return list(out)
-    if not _is_host(inputs) or n <= HOST_CHUNK:
+    if C == 0:
         dev = _device_of(*inputs)
         ins = [_on(t, dev, d) for t, d in zip(inputs, in_dtypes)]
         _check_lengths(n, *ins)
@@ -203,7 +214,7 @@ def _rows_call(name, inputs, in_dtypes, out_dtypes, build_args, out=None):
         for st in streams:
             st.wait_stream(main)
         copied = [None] * len(compute)    # per staging set: its last copy-out
-        for k, (lo, m) in enumerate(_chunks(n)):
+        for k, (lo, m) in enumerate(_chunks(n, C)):
             j = k % len(compute)
             st = compute[j]
             dins, douts = bufs[j]

@@ -25,3 +25,17 @@ def test_ramp_halves_the_first_and_last_chunk(monkeypatch):
     assert sizes[4:-4] == [C] * 6
     monkeypatch.setattr(api, "HOST_RAMP", False)
     assert [m for _, m in api._chunks(8 * C)] == [C] * 8
+
+
+def test_host_chunk_size_by_call_size():
+    """Calls up to HOST_CHUNK / 4 rows take one unpipelined round trip; above, a quarter of the
+    call per chunk (at least HOST_CHUNK / 8), and HOST_CHUNK from 4 HOST_CHUNK rows on."""
+    C = api.HOST_CHUNK
+    assert api._host_chunk(1) == 0 and api._host_chunk(C // 4) == 0
+    assert api._host_chunk(C // 4 + 1) == C // 8
+    assert api._host_chunk(C) == C // 4
+    assert api._host_chunk(2 * C + 3) == -(-(2 * C + 3) // 4)
+    assert api._host_chunk(4 * C) == C and api._host_chunk(16 * C) == C
+    for n in (C // 4 + 1, C, 3 * C + 7):
+        sizes = [m for _, m in api._chunks(n, api._host_chunk(n))]
+        assert sum(sizes) == n and max(sizes) <= api._host_chunk(n)
